@@ -1,0 +1,455 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one oracle function to something other than itself: a worked
+example the paper prints, a closed form, an invariant, a special case that
+reduces to a known function, or brute force. None of these needs a GPU.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import trafficgen as tg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def P(log2_eta, q, r, delta, k, theta, flags=0):
+    return oracle.Params(log2_eta, q, r, delta, k, theta, flags)
+
+
+def identity_tables():
+    """Tables with T_j[b] = b << 8j in both sets: the tabulation hash is then x itself."""
+    t = np.zeros(2048, np.uint32)
+    for s in (0, 1024):
+        for j in range(4):
+            t[s + 256 * j: s + 256 * (j + 1)] = (np.arange(256, dtype=np.uint64) << np.uint64(8 * j)).astype(np.uint32)
+    return t
+
+
+# ------------------------------------------------------------------ hashes
+
+def test_tabulation_reduces_to_identity():
+    """Special case: with T_j[b] = b<<8j, H1(oip) = oip mod eta and RHFG[0](cip) = cip mod 2^q.
+    A wrong byte order, shift or table offset breaks this."""
+    p = P(11, 14, 5, 6, 4, 1024)
+    t = identity_tables()
+    rng = np.random.default_rng(1)
+    for x in list(rng.integers(0, 2**32, 300, dtype=np.uint64)) + [0, 1, 255, 256, 2**24, 2**32 - 1]:
+        x = int(x)
+        assert oracle.h1(p, t, x) == x % 2048
+        assert int(oracle.rhfg(p, t, x)[0]) == x % (1 << 14)
+
+
+def test_rhfg_row_i_only_depends_on_row0_and_window():
+    """Eq. 2-3: RHFG[i](cip) XOR RHFG[0](cip) = B(i) does not depend on the random tables."""
+    p = P(11, 14, 5, 6, 4, 1024)
+    rng = np.random.default_rng(2)
+    ta, tb = tg.hash_tables(5), tg.hash_tables(6)
+    for x in rng.integers(0, 2**32, 200, dtype=np.uint64):
+        ca, cb = oracle.rhfg(p, ta, int(x)), oracle.rhfg(p, tb, int(x))
+        assert np.array_equal(ca[1:] ^ ca[0], cb[1:] ^ cb[0])
+
+
+PARAM_SETS = [
+    P(11, 14, 5, 6, 4, 1024),   # the paper's dimensions: (r-2)*delta+q = 32
+    P(11, 18, 5, 5, 60, 1024),  # q=18: 33 bits of windows
+    P(6, 9, 5, 8, 3, 40),       # tiny: 33 bits, 1-bit overlap
+    P(11, 24, 3, 8, 4, 1024),   # r=3
+    P(11, 16, 4, 8, 4, 1024),   # r=4
+    P(11, 12, 6, 5, 4, 1024),   # r=6
+]
+
+
+@pytest.mark.parametrize("p", PARAM_SETS, ids=lambda p: f"q{p.q}r{p.r}d{p.delta}")
+def test_rhfg_roundtrip_sampled(p):
+    """Every bit of cip appears in some B(i) when (r-2)*delta+q >= 32 (Sec. 3.3): regaining a
+    host from its own tuple gives it back, on 2^22 random values and the edge values."""
+    t = tg.hash_tables(99)
+    rng = np.random.default_rng(p.q * 131 + p.r)
+    xs = rng.integers(0, 2**32, 1 << 22, dtype=np.uint64).astype(np.uint32)
+    edges = np.array([0, 1, 2**31, 2**32 - 1, 0x80000001, 0x7FFFFFFF] + [1 << b for b in range(32)],
+                     dtype=np.uint64).astype(np.uint32)
+    assert oracle.roundtrip_failures(p, t, xs) == 0
+    assert oracle.roundtrip_failures(p, t, edges) == 0
+
+
+@pytest.mark.parametrize("p", PARAM_SETS, ids=lambda p: f"q{p.q}r{p.r}d{p.delta}")
+def test_overlap_property_of_true_tuples(p):
+    """Sec. 3.3: the high q-delta bits of B(i) equal the low q-delta bits of B(i+1)."""
+    t = tg.hash_tables(3)
+    rng = np.random.default_rng(7)
+    w = p.q - p.delta
+    for x in rng.integers(0, 2**32, 500, dtype=np.uint64):
+        c = oracle.rhfg(p, t, int(x)).astype(np.int64)
+        B = c ^ c[0]
+        for i in range(2, p.r):
+            assert (B[i - 1] >> p.delta) == (B[i] & ((1 << w) - 1))
+
+
+def test_extract_rejects_window_bits_beyond_32():
+    """Tiny dims cover 33 bits: a tuple whose last window has bit 32 set names no IPv4 host."""
+    p = P(6, 9, 5, 8, 3, 40)
+    t = tg.hash_tables(4)
+    x = 0xDEADBEEF
+    c = oracle.rhfg(p, t, x).astype(np.uint32)
+    assert oracle.extract(p, c) == x
+    bad = c.copy()
+    bad[4] ^= np.uint32(1 << 8)   # B(4) covers bits 24..32; bit 8 of B(4) is bit 32 of cip
+    assert oracle.extract(p, bad) is None
+    worse = c.copy()
+    worse[2] ^= np.uint32(1)      # breaks the B(1)/B(2) overlap
+    assert oracle.extract(p, worse) is None
+
+
+def test_bit_coverage_condition_is_needed():
+    """With (r-2)*delta+q < 32 some bit of cip is in no window, and check_params refuses it."""
+    assert oracle.check_params(P(11, 14, 5, 6, 4, 1024))
+    assert not oracle.check_params(P(11, 13, 5, 6, 4, 1024))
+    assert not oracle.check_params(P(11, 14, 5, 14, 4, 1024))  # delta < q
+    assert not oracle.check_params(P(11, 14, 5, 6, 65535, 1024))
+    assert oracle.check_params(P(11, 14, 5, 6, 65534, 1024))
+
+
+# ---------------------------------------------------------------- threshold
+
+@pytest.mark.parametrize("eta,theta", [(2048, 1024), (64, 40), (2048, 1), (2048, 5000), (32768, 1024),
+                                       (256, 1024), (4096, 333)])
+def test_threshold_is_eq1_inverse(eta, theta):
+    """Sec. 3.3 defines R^_k so that Eq. 1 with z0 = eta - R^_k estimates exactly theta; the
+    integer threshold is the first R_k whose Eq. 1 estimate reaches theta."""
+    thr, rhat = oracle.threshold(eta, theta)
+    assert math.isclose(-eta * math.log((eta - rhat) / eta), theta, rel_tol=1e-12)
+    assert thr - 1 < rhat <= thr
+    assert oracle.estimate(eta, thr) >= theta
+    assert oracle.estimate(eta, thr - 1) < theta
+
+
+def test_paper_parameters(golden):
+    g = golden["experiment_parameters"]
+    p = P(int(math.log2(g["eta"])), g["q"], g["r"], g["delta"], 4, g["theta"])
+    assert 1 << p.log2_eta == g["eta"]
+    assert oracle.check_params(p)
+    assert (p.r - 2) * p.delta + p.q == 32
+    b = golden["pair_buffer"]
+    assert b["alpha"] == g["alpha"] and b["alpha"] * b["bytes_per_pair"] == b["kilobytes"] * 1024
+    lw = golden["longest_window"]
+    assert oracle.check_params(P(11, 14, 5, 6, lw["k_max"], 1024))
+    assert not oracle.check_params(P(11, 14, 5, 6, lw["k_max"] + 1, 1024))
+    assert round(lw["k_max"] / 3600, 1) == lw["hours_at_one_second_slots"]
+
+
+def test_linear_counting_estimate_tracks_distinct_count():
+    """Eq. 1 on one estimator fed m distinct opposite hosts estimates m (linear counting)."""
+    p = P(11, 14, 5, 6, 1, 1024)
+    t = tg.hash_tables(21)
+    rng = np.random.default_rng(5)
+    for m in (200, 1000, 3000):
+        sk = oracle.new_sketch(p)
+        oips = rng.choice(2**32, size=m, replace=False).astype(np.uint32)
+        pairs = np.stack([np.full(m, 0x0A000001, np.uint32), oips], axis=1)
+        oracle.scan(p, t, sk, pairs)
+        col = int(oracle.rhfg(p, t, 0x0A000001)[0])
+        rk = int(oracle.rk_row(p, sk, 0)[col])
+        est = oracle.estimate(p.eta, rk)
+        assert abs(est - m) < 0.1 * m, (m, rk, est)
+
+
+# ------------------------------------------------------------------ sketch
+
+def _recorder_index(p, t, cip, oip):
+    cols = oracle.rhfg(p, t, cip)
+    d = oracle.h1(p, t, oip)
+    return [((i << p.q) + int(cols[i])) * p.eta + d for i in range(p.r)]
+
+
+def _random_slots(rng, nslots, n, nsrc, peers):
+    srcs = rng.integers(0, 2**32, nsrc, dtype=np.uint64).astype(np.uint32)
+    out = []
+    for _ in range(nslots):
+        cnt = int(rng.integers(0, n + 1))
+        s = srcs[rng.integers(0, nsrc, cnt)]
+        o = rng.integers(0, peers, cnt).astype(np.uint32) * np.uint32(2654435761)
+        out.append(np.stack([s, o], axis=1).astype(np.uint32))
+    return out
+
+
+def test_sketch_matches_closed_form():
+    """Sec. 3.2: after slot t every recorder equals min(65535, t - s), s being the last slot in
+    which some pair set it to 0 (65535 if never). Checked at every slot of a random stream."""
+    p = P(5, 9, 5, 8, 3, 10)
+    t = tg.hash_tables(8)
+    rng = np.random.default_rng(11)
+    slots = _random_slots(rng, 12, 300, 40, 5000)
+    sk = oracle.new_sketch(p)
+    last = np.full(sk.size, -1, dtype=np.int64)
+    for ts, pairs in enumerate(slots):
+        if ts:
+            oracle.advance(p, sk)
+        oracle.scan(p, t, sk, pairs)
+        for cip, oip in pairs:
+            for idx in _recorder_index(p, t, int(cip), int(oip)):
+                last[idx] = ts
+        expect = np.where(last < 0, 65535, np.minimum(65535, ts - last)).astype(np.uint16)
+        assert np.array_equal(sk, expect), ts
+
+
+def test_saturation_and_longest_window():
+    """Recorders never pass 65535 (Sec. 3.2): after 65535 advances a recorder set at slot 0 reads
+    65535 and stays there; one set at slot 1 reads 65534 = k_max, which is outside the window."""
+    p = P(1, 6, 8, 5, 65534, 1)
+    t = tg.hash_tables(9)
+    sk = oracle.new_sketch(p)
+    pa = np.array([[0x01020304, 77]], np.uint32)
+    pb = np.array([[0x0A0B0C0D, 99]], np.uint32)
+    oracle.scan(p, t, sk, pa)
+    ia = _recorder_index(p, t, 0x01020304, 77)
+    ib = _recorder_index(p, t, 0x0A0B0C0D, 99)
+    oracle.advance(p, sk)
+    oracle.scan(p, t, sk, pb)
+    for _ in range(65534):
+        oracle.advance(p, sk)
+    assert all(sk[i] == 65535 for i in ia if i not in ib)
+    assert all(sk[i] == 65534 for i in ib)
+    assert all(oracle.rk_row(p, sk, r).sum() == 0 for r in range(p.r))  # 65534 is not < k
+    for _ in range(3):
+        oracle.advance(p, sk)
+    assert sk.max() == 65535 and sk.min() == 65535
+
+
+def test_scan_is_order_free():
+    """Setting a recorder to 0 is idempotent (Sec. 4.1): any permutation of the pairs gives the
+    same RSEA."""
+    p = P(11, 14, 5, 6, 4, 1024)
+    t = tg.hash_tables(12)
+    pairs = tg.traffic_for("paper_c1").fill(0, n=20000)
+    a, b = oracle.new_sketch(p), oracle.new_sketch(p)
+    oracle.scan(p, t, a, pairs)
+    oracle.scan(p, t, b, pairs[np.random.default_rng(0).permutation(len(pairs))])
+    assert np.array_equal(a, b)
+
+
+def test_slice_leaving_window_stops_counting():
+    """A slot's pairs count for exactly k slots: k-1 advances later they are in R_k, k later not."""
+    p = P(11, 14, 5, 6, 4, 1024)
+    t = tg.hash_tables(13)
+    sk = oracle.new_sketch(p)
+    pairs = tg.traffic_for("paper_c1").fill(0, n=5000)
+    oracle.scan(p, t, sk, pairs)
+    for _ in range(p.k - 1):
+        oracle.advance(p, sk)
+    assert sum(int(oracle.rk_row(p, sk, r).sum()) for r in range(p.r)) > 0
+    oracle.advance(p, sk)
+    assert sum(int(oracle.rk_row(p, sk, r).sum()) for r in range(p.r)) == 0
+
+
+def test_min_merge_equals_single_sketch_of_all_pairs():
+    """Distributed equivalence (Sec. 4, Algorithm 5 with the min reading): n routers' sketches,
+    each advanced every slot, merge into the sketch one router would hold had it seen every pair.
+    Min commutes with the saturating +1. The literal max merge keeps only recorders seen by every
+    router and does not."""
+    p = P(8, 12, 6, 5, 3, 100)
+    t = tg.hash_tables(14)
+    rng = np.random.default_rng(3)
+    R = 4
+    routers = [oracle.new_sketch(p) for _ in range(R)]
+    single = oracle.new_sketch(p)
+    for ts in range(7):
+        if ts:
+            for sk in routers + [single]:
+                oracle.advance(p, sk)
+        for sk in routers:
+            pr = _random_slots(rng, 1, 2000, 200, 100000)[0]
+            oracle.scan(p, t, sk, pr)
+            oracle.scan(p, t, single, pr)
+        assert np.array_equal(oracle.merge(p, routers), single)
+    pmax = P(8, 12, 6, 5, 3, 100, oracle.MAX_MERGE)
+    assert not np.array_equal(oracle.merge(pmax, routers), single)
+
+
+# ------------------------------------------------------------------ regain
+
+def _pipeline_states(name, nslots):
+    W = tg.workload(name)
+    p = oracle.params(W["params"])
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    pipe = oracle.Pipeline(p, tabs, T.routers)
+    for ts in range(nslots):
+        pipe.step(T.slot(ts), regain_method=None)
+        yield p, tabs, pipe.global_sk, T
+
+
+@pytest.mark.parametrize("name,nslots", [("tiny", 8), ("paper_c1", 5)])
+def test_recursive_and_levelwise_regain_agree(name, nslots):
+    """Algorithms 3-4 (recursive) and 6-7 (level by level) are written separately; they must give
+    the same list, the same R_k and the same candidate count at every row. The pruned form must
+    give the same list."""
+    for p, tabs, gsk, _ in _pipeline_states(name, nslots):
+        for flags in (0, oracle.VERIFY_H0):
+            pp = oracle.Params(*[getattr(p, f) for f in ("log2_eta", "q", "r", "delta", "k", "theta")], flags)
+            a = oracle.regain(pp, tabs, gsk, "recursive")
+            b = oracle.regain(pp, tabs, gsk, "levelwise")
+            c = oracle.regain(pp, tabs, gsk, "pruned")
+            assert np.array_equal(a["ips"], b["ips"]) and np.array_equal(a["rk"], b["rk"])
+            assert np.array_equal(a["levels"], b["levels"])
+            assert np.array_equal(b["ips"], c["ips"]) and np.array_equal(b["rk"], c["rk"])
+            assert np.all(np.diff(b["ips"].astype(np.int64)) > 0)
+
+
+_BF = None
+
+
+def _bruteforce_lib():
+    global _BF
+    if _BF is None:
+        out = os.path.join(ROOT, "tests", "_build", "libbrute.so")
+        src = os.path.join(ROOT, "tests", "brute_force.c")
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", out + ".tmp", src])
+            os.replace(out + ".tmp", out)
+        _BF = ctypes.CDLL(out)
+        _BF.bf_enumerate.restype = ctypes.c_uint64
+    return _BF
+
+
+class _BfIn(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("log2_eta", "q", "r", "delta", "k", "thr")] + \
+               [("tables", ctypes.c_void_p), ("hot", ctypes.c_void_p), ("bitmaps", ctypes.c_void_p)]
+
+
+def bruteforce(p, tabs, sk, verify):
+    """All hosts in [0, 2^32) the definitions list, computed forward (see brute_force.c)."""
+    thr, _ = oracle.threshold(p.eta, p.theta)
+    below = (sk.reshape(p.r, p.C, p.eta) < p.k)
+    rk = below.sum(axis=2)
+    hot = (rk >= thr).astype(np.uint8)
+    bm = np.packbits(below, axis=2, bitorder="little").view(np.uint32)
+    bm = np.ascontiguousarray(bm)
+    h0 = np.nonzero(hot[0])[0].astype(np.uint32)
+    tabs = np.ascontiguousarray(tabs, np.uint32)
+    cap = 1 << 20
+    xs = np.empty(cap, np.uint32)
+    rks = np.empty(cap, np.uint32)
+    bi = _BfIn(p.log2_eta, p.q, p.r, p.delta, p.k, thr, tabs.ctypes.data, hot.ctypes.data, bm.ctypes.data)
+    n = _bruteforce_lib().bf_enumerate(ctypes.byref(bi), int(verify), ctypes.c_void_p(h0.ctypes.data),
+                                       ctypes.c_uint32(h0.size), ctypes.c_void_p(xs.ctypes.data),
+                                       ctypes.c_void_p(rks.ctypes.data), ctypes.c_uint64(cap))
+    assert n <= cap
+    order = np.argsort(xs[:n])
+    return xs[:n][order], rks[:n][order]
+
+
+def _dense_tiny():
+    """tiny dimensions with twelve planted hosts: many hot estimators, so with the 1-bit overlap
+    the candidate tuples include many hosts' columns."""
+    W = tg.workload("tiny")
+    W["traffic"].update(n_planted=12, count_a=400)
+    return W
+
+
+@pytest.mark.slow
+def test_regain_equals_bruteforce_over_all_ipv4():
+    """Exhaustive pin: over every IPv4 value, the regained list equals the forward definition,
+    with and without the RHFG[0] check."""
+    for W in (tg.workload("tiny"), _dense_tiny()):
+        p0 = oracle.params(W["params"])
+        tabs = tg.hash_tables(W["hash_seed"])
+        T = tg.Traffic(**W["traffic"])
+        pipe = oracle.Pipeline(p0, tabs, T.routers)
+        for ts in range(4):
+            pipe.step(T.slot(ts), regain_method=None)
+        for verify in (True, False):
+            p = oracle.params(W["params"], oracle.VERIFY_H0 if verify else 0)
+            got = oracle.regain(p, tabs, pipe.global_sk, "levelwise")
+            bx, brk = bruteforce(p, tabs, pipe.global_sk, verify)
+            assert np.array_equal(got["ips"], bx)
+            assert np.array_equal(got["rk"], brk)
+            assert len(bx) > 0
+
+
+# ---------------------------------------------------------- precise algorithm
+
+def test_precise_algorithm_paper_example(golden):
+    g = golden["precise_algorithm_example"]
+    names = {}
+    ids = lambda s: names.setdefault(s, len(names) + 1)  # noqa: E731
+    pairs = np.array([[ids(a), ids(b)] for a, b in g["pairs"]], np.uint32)
+    ex = oracle.Exact(k=1, theta=1)
+    ex.add_slot(pairs)
+    ips, deg = ex.report()
+    assert list(ips) == [ids("cip")] and list(deg) == [g["opposite_number"]]
+    # the unsynchronised count the example warns about is the number of pairs inserted blindly
+    assert len(g["pairs"]) == g["unsynchronised_parallel_count"]
+
+
+def test_sliding_window_paper_example(golden):
+    """Sec. 3.1: theta peers only in S5, k = 5 -> reported in SSP(1,5)..SSP(5,5) and, under
+    discrete windows of the same length starting at S0, only in the second window."""
+    g = golden["sliding_window_example"]
+    k, theta, s5 = g["k"], 8, g["active_slot"]
+    host = 0x0A000001
+    ex = oracle.Exact(k=k, theta=theta)
+    reported = []
+    for ts in range(15):
+        pr = np.array([[host, 1000 + j] for j in range(theta)], np.uint32) if ts == s5 else \
+            np.array([[0x0B000000 + ts, 7]], np.uint32)
+        ex.add_slot(pr)
+        ips, _ = ex.report()
+        if host in ips:
+            reported.append(ts - k + 1)   # window SW(i, k) ends at slot i+k-1
+    assert reported == g["sliding_windows_reporting"]
+    dis = oracle.Exact(k=1, theta=theta)  # discrete window of k slots: one merged slot per window
+    rep = []
+    for w in range(3):
+        slots = [np.array([[host, 1000 + j] for j in range(theta)], np.uint32) if ts == s5 else
+                 np.zeros((0, 2), np.uint32) for ts in range(w * k, (w + 1) * k)]
+        dis.add_slot(np.concatenate(slots))
+        if host in dis.report()[0]:
+            rep.append(w)
+    assert rep == g["discrete_window_reporting"]
+
+
+def test_sliding_example_through_the_sketch(golden):
+    """The same example through the sliding estimator array: the host is regained at the end of
+    S5..S9 and not before or after (2*theta peers keep the estimate clear of the threshold)."""
+    g = golden["sliding_window_example"]
+    k = g["k"]
+    p = P(11, 14, 5, 6, k, 1024)
+    tabs = tg.hash_tables(31)
+    host = 0xC0A80101
+    pipe = oracle.Pipeline(p, tabs, 1)
+    seen = []
+    for ts in range(13):
+        pr = np.array([[host, 0x50000000 + j] for j in range(2 * p.theta)], np.uint32) if ts == g["active_slot"] \
+            else np.zeros((0, 2), np.uint32)
+        res = pipe.step([pr])
+        if host in res["ips"]:
+            seen.append(ts - k + 1)
+    assert seen == g["sliding_windows_reporting"]
+
+
+def test_precise_counter_bruteforce():
+    """Exact counter against recomputing each window's distinct pairs from scratch."""
+    rng = np.random.default_rng(17)
+    k, theta = 3, 5
+    slots = _random_slots(rng, 10, 120, 6, 40)
+    ex = oracle.Exact(k=k, theta=theta)
+    for ts in range(len(slots)):
+        ex.add_slot(slots[ts])
+        ips, deg = ex.report()
+        window = set()
+        for s in range(max(0, ts - k + 1), ts + 1):
+            window |= {(int(a), int(b)) for a, b in slots[s]}
+        counts = {}
+        for a, _ in window:
+            counts[a] = counts.get(a, 0) + 1
+        expect = sorted((a, c) for a, c in counts.items() if c >= theta)
+        assert list(zip(ips.tolist(), deg.tolist())) == expect
+        for a, c in counts.items():
+            assert ex.degree(a) == c
