@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the sliding super point detector's hot path on one GB300 per rank.
+
+One step = one time slot of the whole path on the workload's routers: scan the
+slot's packets (Algorithm 2), then close the slot - merge, hot-estimator
+extraction and window advance in one streaming pass, candidate levels, final
+test and the sorted list. Inputs are resident in HBM before timing; every step
+scans a distinct slice, and the 5 GiB RSEA streamed every step is far larger
+than L2. `e2e` repeats the steps through the C ABI from pinned host buffers
+(host->device pair copies and the device->host list read inside the timed
+region).
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Under torchrun each rank runs an independent replica (its own traffic seed) on
+its own GPU; rank 0 prints one JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scan Mpps (Gb/s @800B) + reconstruct ms/slice, batched vs plain, 1 GB300"
+DEFAULT_WORKLOAD = "corelink_c2"
+PAPER_PACKET_BYTES = 800
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--fill", type=int, default=-1, help="untimed slots before warm-up (default: k)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, local):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- misc
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("ssd_stream.cu", "ssd_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1803_11036_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the streaming pass from the committed ncu summary, if the
+    kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"close_pass_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def gbps(mpps: float):
+    return {"si": round(mpps * PAPER_PACKET_BYTES * 8 / 1000, 2),
+            "paper_convention": round(mpps * PAPER_PACKET_BYTES * 8 / 1024, 2)}
+
+
+# ---------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(W: dict):
+    """A bounded sample of the workload for the single-threaded oracle: the same recipe with
+    2^4 fewer columns and 2^4 fewer packets per slot, which keeps the recorder bytes per packet
+    (the advance and merge passes) equal to the full workload's."""
+    import trafficgen as tg
+    S = tg.workload(W["_name"]) if "_name" in W else W
+    S = json.loads(json.dumps(S))
+    prm = S["params"]
+    q = prm["q"] - 4
+    r = prm["r"]
+    delta = max(1, -(-(32 - q) // (r - 2)))
+    prm.update(q=q, delta=delta)
+    tr = S["traffic"]
+    if tr.get("count") == "fixed":
+        tr["count_a"] = max(1, tr["count_a"] >> 4)
+    elif tr.get("count") == "split":
+        tr["count_a"] = max(1, tr["count_a"] >> 4)
+    tr["n_src"] = max(1, tr["n_src"] >> 4)
+    desc = (f"{W.get('_name', 'workload')} recipe at 1/16 scale: q={q}, delta={delta}, "
+            f"{tr.get('count_a')} packets/slot/router, {tr['n_src']} sources; advance+scan+merge+regain per slot")
+    return S, desc
+
+
+class OracleSlots:
+    def __init__(self, W: dict):
+        import oracle
+        import trafficgen as tg
+        S, self.desc = oracle_sample(W)
+        self.p = oracle.params(S["params"])
+        self.tabs = tg.hash_tables(S["hash_seed"])
+        self.T = tg.Traffic(**S["traffic"])
+        self.pipe = oracle.Pipeline(self.p, self.tabs, self.T.routers)
+        self.t = 0
+
+    def step(self) -> int:
+        pairs = self.T.slot(self.t)
+        self.t += 1
+        self.pipe.step(pairs, "pruned")
+        return sum(len(x) for x in pairs)
+
+
+def cpu_baseline(W: dict, budget_s: float = 12.0, min_slots: int = 3) -> dict:
+    o = OracleSlots(W)
+    pk, slots = 0, 0
+    t0 = time.perf_counter()
+    while slots < min_slots or time.perf_counter() - t0 < budget_s:
+        pk += o.step()
+        slots += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(pk / dt / 1e6, 4), "unit": "Mpps", "cores": 1, "kind": "oracle",
+            "sample": f"{slots} slots of {o.desc}", "seconds": round(dt, 2),
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args, world, rank):
+    """The oracle, as it stands, as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import trafficgen as tg
+    W = tg.workload(args.workload)
+    W["_name"] = args.workload
+    o = OracleSlots(W)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    pk = 0
+    for _ in range(args.steps):
+        pk += o.step()
+    dt = time.perf_counter() - t0
+    v = pk / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mpps", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": o.desc},
+            "cpu_baseline": {"value": round(v, 4), "unit": "Mpps", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} slots of {o.desc}"},
+            "e2e": {"value": round(v, 4), "unit": "Mpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1803_11036_gb300 as ssd
+    import trafficgen as tg
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W = tg.workload(args.workload)
+    W["_name"] = args.workload
+    if rank:
+        W["traffic"]["seed"] += 7919 * rank   # an independent replica per rank
+    prm = W["params"]
+    k = prm["k"]
+    fill = k if args.fill < 0 else args.fill
+    T = tg.Traffic(**W["traffic"])
+    R = T.routers
+    nslots = fill + args.warmup + args.steps
+
+    # ---- inputs resident in HBM: every slot's packets, generated in chunks
+    slot_dev = []
+    chunk = 8
+    for s0 in range(0, nslots, chunk):
+        jobs = [(t, r) for t in range(s0, min(nslots, s0 + chunk)) for r in range(R)]
+        views = T.fill_many(jobs)
+        for i in range(0, len(views), R):
+            slot_dev.append([torch.from_numpy(v.reshape(-1).view(np.int32)).to(dev) for v in views[i:i + R]])
+    pk_per_slot = [sum(x.numel() // 2 for x in s) for s in slot_dev]
+
+    ctx = ssd.Context(ssd.make_params(prm), tg.hash_tables(W["hash_seed"]), device=local)
+    routers = [ctx.sketch() for _ in range(R)]
+    stream = torch.cuda.Stream(dev)
+    cap = 1 << 16
+    ips = torch.empty(cap, dtype=torch.int32, device=dev)
+    rks = torch.empty(cap, dtype=torch.int32, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step(t, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        if R == 1:
+            ctx.scan(routers[0], slot_dev[t][0], stream=stream)
+        else:
+            ctx.scan_batch(routers, slot_dev[t], stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.close_slot(routers, None, out=(ips, rks, n_out), stream=stream, sync=False)
+
+    with torch.cuda.stream(stream):
+        for t in range(fill + args.warmup):
+            step(t)
+    stream.synchronize()
+    st_fill = ctx.stats(stream)
+    if st_fill["status"]:
+        raise RuntimeError(f"capacity status {st_fill['status']} during fill")
+
+    # ---- timed region
+    E = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for i in range(args.steps):
+            e = E[i]
+            ctx.set_trace(e[2], e[3], e[4])
+            step(fill + args.warmup + i, ev=e)
+        t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ctx.set_trace()
+    launches = ctx.launch_count - launches0
+    st = ctx.stats(stream)
+    if st["status"]:
+        raise RuntimeError(f"capacity status {st['status']} in the timed region")
+
+    total_ms = t_start.elapsed_time(t_end)
+    scan_ms = [E[i][0].elapsed_time(E[i][1]) for i in range(args.steps)]
+    pass_ms = [E[i][2].elapsed_time(E[i][3]) for i in range(args.steps)]
+    tail_ms = [E[i][3].elapsed_time(E[i][4]) for i in range(args.steps)]
+    timed_pk = sum(pk_per_slot[fill + args.warmup:])
+    max_ms = max_over_ranks(total_ms, world)
+    all_pk = sum_over_ranks(timed_pk, world)
+    value = all_pk / (max_ms / 1e3) / 1e6
+    scan_mpps = timed_pk / (sum(scan_ms) / 1e3) / 1e6
+
+    eta, C, r = 1 << prm["log2_eta"], 1 << prm["q"], prm["r"]
+    recorders = eta * C * r
+    pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
+    avg_pass_s = statistics.mean(pass_ms) / 1e3
+    achieved = pass_bytes / avg_pass_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = profiled_traffic(args.workload)
+    scan_alg_bytes = 8 + 2 * r                  # pair read + r recorder writes per packet
+
+    # ---- end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = [[torch.from_numpy(x.cpu().numpy()).pin_memory() for x in s]
+                for s in slot_dev[fill + args.warmup - 1:]]
+        d2h = 0
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for j in range(len(host)):   # j = 0 is an untimed warm-up of the host path
+                if j == 1:
+                    ea.record(stream)
+                for sk, h in zip(routers, host[j]):
+                    ctx.scan_host(sk, h, stream=stream)
+                ctx.close_slot(routers, None, out=(ips, rks, n_out), stream=stream, sync=False)
+                m = int(n_out.item())
+                lst = (ips[:m].cpu(), rks[:m].cpu())
+                if j >= 1:
+                    d2h += 8 + 8 * len(lst[0])
+            eb.record(stream)
+        stream.synchronize()
+        e2e_ms = ea.elapsed_time(eb)
+        e2e_ms = max_over_ranks(e2e_ms, world)
+        e2e = {"value": round(all_pk / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mpps",
+               "h2d_bytes_per_step": int(8 * timed_pk / args.steps),
+               "d2h_bytes_per_step": int(d2h / args.steps)}
+        del host
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline(W)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpps", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": args.workload, "routers": R, "packets_per_slot": int(pk_per_slot[-1]),
+                   "k": k, "eta": eta, "q": prm["q"], "r": r, "delta": prm["delta"], "theta": prm["theta"],
+                   "window_filled_slots": fill, "l2": "inputs larger than L2: the 5 GiB RSEA is streamed every "
+                   "step and each step scans a distinct slice"},
+        "gbps_at_800B": gbps(value),
+        "scan": {"mpps": round(scan_mpps, 2), "gbps_at_800B": gbps(scan_mpps),
+                 "ms_per_slice": round(statistics.mean(scan_ms), 4),
+                 "achieved_gbs_algorithmic": round(scan_alg_bytes * timed_pk / (sum(scan_ms) / 1e3) / 1e9, 1)},
+        "reconstruct_ms_per_slice": {"close_pass": round(statistics.mean(pass_ms), 4),
+                                     "candidates_and_list": round(statistics.mean(tail_ms), 4),
+                                     "total": round(statistics.mean(pass_ms) + statistics.mean(tail_ms), 4)},
+        "batched_vs_plain": None,
+        "roofline": {"kernel": "k_stream_large<one router, advance, hot> (merge + hot extraction + advance)",
+                     "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": pass_bytes,
+                     "traffic": traffic},
+        "hot_per_row": st["hot"], "candidates_per_level": st["level"], "list_size": st["n_out"],
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    dist_init(world, local)
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * ssd.h - C ABI of the GB300 sliding super point detector.
+ *
+ * Sliding super point detection from distributed edge routers (arXiv
+ * 1803.11036): every router scans the <cip, oip> IPv4 pairs of each time slot
+ * into its own reversible sliding estimator array (RSEA); at the end of a slot
+ * the routers' arrays are merged and the sliding super points - hosts with at
+ * least theta distinct opposite hosts within the last k slots (Def. 2-4) - are
+ * regained through the reversible hash functions group (RHFG).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers on the context's device; pointers
+ *    marked "host or device" may be either (unified addressing). The caller
+ *    owns every buffer it passes; the library owns contexts, sketches and the
+ *    scratch memory a context allocates at creation.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls enqueue work on it and return without waiting unless they
+ *    say otherwise. Work for one context must not run on two streams at once:
+ *    a context holds one set of scratch buffers.
+ *  - Every call returns SSD_OK (0) or a negative SSD_E* code; no exception or
+ *    abort crosses the ABI. On SSD_EINVAL nothing was enqueued.
+ *  - Packet pairs are uint32 pairs laid out (cip, oip), 8 bytes per packet,
+ *    host-order IPv4 values (Sec. 3.1). A pair buffer must be 8-byte aligned.
+ *  - A sketch is r rows x 2^q columns of sliding estimators, each eta = 2^log2_eta
+ *    uint16 distance recorders, stored row-major: recorder j of estimator
+ *    (row, col) is element ((row * 2^q) + col) * eta + j (Sec. 3.3).
+ */
+#ifndef SSD_H
+#define SSD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSD_API __attribute__((visibility("default")))
+#else
+#define SSD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define SSD_OK 0
+#define SSD_EINVAL (-1)    /* bad argument or parameter set */
+#define SSD_ENOMEM (-2)    /* device allocation failed */
+#define SSD_ECAPACITY (-3) /* a capacity was exceeded; see ssd_stats */
+#define SSD_ECUDA (-4)     /* a CUDA call failed; ssd_last_cuda_error() names it */
+#define SSD_ETIMEOUT (-5)  /* reserved: a bounded device-side wait ran out */
+#define SSD_ESTATE (-6)    /* sketches disagree on their slot, or belong to another context */
+
+/* ------------------------------------------------------------------ flags */
+/* Also require RHFG[0](cip) == he_0 of the tuple a host is regained from. The
+ * paper does not make this check (Algorithm 4 extracts the host directly);
+ * without it a tuple mixing several hosts' estimators can name a host that is
+ * not there. Off by default. */
+#define SSD_VERIFY_H0 1u
+/* Do not prune partial candidate tuples by their union's R_k: run the candidate
+ * levels literally (Algorithms 6-7). The list is identical either way; only the
+ * candidate counts (and the work) differ. */
+#define SSD_NO_PRUNE 2u
+
+#define SSD_MAX_R 8
+#define SSD_MAX_ROUTERS 128
+
+/* Detector parameters (Sec. 3.2-3.3, Sec. 5).
+ *   eta = 2^log2_eta recorders per estimator, 5 <= log2_eta <= 15
+ *   2^q columns, r rows, shift step delta:
+ *       3 <= r <= SSD_MAX_R, 0 < delta < q <= 24, (r-2)*delta + q >= 32 (Eq. 2-3)
+ *   k: window length in slots, 1 <= k <= 65534 (Sec. 3.2)
+ *   theta: super point threshold (Def. 2), >= 1
+ *   flags: SSD_VERIFY_H0 | SSD_NO_PRUNE
+ *   hse_capacity: hot estimators kept per row (0 = min(2^q, 65536))
+ *   ctb_capacity: tuples per candidate tuple buffer (0 = 2^22)
+ *   out_capacity: accepted tuples staged before the list is sorted (0 = 2^20)
+ */
+typedef struct ssd_params {
+  uint32_t log2_eta;
+  uint32_t q;
+  uint32_t r;
+  uint32_t delta;
+  uint32_t k;
+  uint32_t theta;
+  uint32_t flags;
+  uint32_t hse_capacity;
+  uint64_t ctb_capacity;
+  uint64_t out_capacity;
+} ssd_params;
+
+typedef struct ssd_ctx ssd_ctx;
+typedef struct ssd_sketch ssd_sketch;
+
+/* Counters of the last regain or slot close of a context. */
+#define SSD_STATUS_HSE_OVERFLOW 1u  /* more hot estimators in a row than hse_capacity */
+#define SSD_STATUS_CTB_OVERFLOW 2u  /* more candidate tuples than ctb_capacity */
+#define SSD_STATUS_OUT_OVERFLOW 4u  /* more accepted tuples than out_capacity */
+#define SSD_STATUS_LIST_OVERFLOW 8u /* more hosts than the caller's list capacity */
+typedef struct ssd_stats {
+  uint32_t status;           /* OR of SSD_STATUS_* */
+  uint32_t threshold;        /* ceil(R^_k), R^_k = eta * (1 - exp(-theta/eta)) (Sec. 3.3) */
+  uint64_t hot[SSD_MAX_R];   /* |HSE(i)|: hot estimators of row i, all of them */
+  uint64_t level[SSD_MAX_R]; /* candidates covering rows 0..i: level[1] pairs, level[2] the
+                                CT_2 triples of Algorithm 6, level[i>2] Algorithm 7's tuples */
+  uint64_t raw;              /* full tuples accepted by the final test, before dedupe */
+  uint64_t n_out;            /* hosts in the sliding super point list */
+} ssd_stats;
+
+/* Validate a parameter set (host only, no GPU needed). SSD_OK or SSD_EINVAL. */
+SSD_API int ssd_params_check(const ssd_params* p);
+
+/* ceil(eta * (1 - exp(-theta/eta))), the integer R_k at which an estimator is
+ * hot (Sec. 3.3), computed in double on the host (no GPU needed). SSD_EINVAL if
+ * the real threshold lies within 1e-9 of an integer. */
+SSD_API int ssd_threshold(const ssd_params* p, uint32_t* thr);
+
+/* Create a context on `device`. `tables` (host) holds 2048 uint32 words: the
+ * simple-tabulation tables of H1 (words 0..1023: T0..T3, 256 each; Sec. 3.2)
+ * followed by those of RHFG[0] (words 1024..2047; Sec. 3.3). The context
+ * copies them, computes the threshold and allocates its scratch (hot-estimator
+ * pools, candidate tuple buffers CTB_1/CTB_2 of Sec. 4.2, the list staging
+ * buffer). Returns SSD_EINVAL, SSD_ENOMEM or SSD_ECUDA on failure (*out = NULL). */
+SSD_API int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx** out);
+SSD_API void ssd_destroy(ssd_ctx* ctx);
+
+/* One RSEA (a router's, or the global one), every recorder set to 65535
+ * (Sec. 3.2), slot counter 0. Synchronous. A sketch may be destroyed before or
+ * after its context, but no call may use it once the context is gone. */
+SSD_API int ssd_sketch_create(ssd_ctx* ctx, ssd_sketch** out);
+SSD_API void ssd_sketch_destroy(ssd_sketch* s);
+/* Bytes of one RSEA: r * 2^q * eta * 2. */
+SSD_API uint64_t ssd_sketch_bytes(const ssd_ctx* ctx);
+/* Slots the sketch has advanced since creation or import. */
+SSD_API int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot);
+/* Copy `count` recorders starting at recorder `first` to dst (host or device).
+ * Waits for `stream` before returning. Checkpointing a sketch is
+ * export + ssd_sketch_slot; resuming is import. */
+SSD_API int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream);
+/* Overwrite the whole sketch from src (host or device; ssd_sketch_bytes bytes)
+ * and set its slot counter. Waits for `stream` before returning. */
+SSD_API int ssd_sketch_import(ssd_sketch* s, const uint16_t* src, uint64_t slot, void* stream);
+
+/* Algorithm 2 for every pair of d_pairs[0 .. 2*n_pairs): DRidx = H1(oip); for
+ * each row i the recorder DRidx of estimator RSEA[i, RHFG[i](cip)] is set to 0,
+ * with RHFG[i](cip) = ((cip >> (i-1)*delta) XOR RHFG[0](cip)) mod 2^q for
+ * i >= 1 (Eq. 2). Order-free and idempotent (Sec. 4.1). n_pairs may be 0. */
+SSD_API int ssd_scan(ssd_sketch* s, const uint32_t* d_pairs, uint64_t n_pairs, void* stream);
+
+/* Algorithm 2 on pairs held in HOST memory (pinned or pageable): the pairs go
+ * over the host link into a context-owned device buffer of `alpha` pairs
+ * (Sec. 4.1; two such buffers, allocated on the first call, 2^22 pairs each)
+ * and each filled buffer is scanned while the next one is copied. Copies run
+ * on an internal stream ordered against `stream`; scans run on `stream`. With
+ * pinned memory the call returns before the copies finish: keep h_pairs
+ * unchanged until `stream` has reached this point. The first call on a
+ * context allocates; make it before any stream capture. */
+SSD_API int ssd_scan_host(ssd_sketch* s, const uint32_t* h_pairs, uint64_t n_pairs, void* stream);
+
+/* Algorithm 2 for n routers in one launch: router j scans d_pairs[j] (n_pairs[j]
+ * packets) into sketches[j]. sketches, d_pairs and n_pairs are host arrays of n
+ * entries, n <= SSD_MAX_ROUTERS; the sketches share one context (an entry may
+ * repeat). Same result as n calls of ssd_scan. */
+SSD_API int ssd_scan_batch(ssd_sketch* const* sketches, const uint32_t* const* d_pairs, const uint64_t* n_pairs,
+                   int n, void* stream);
+
+/* Window advance (Sec. 3.2, Sec. 4.3): every recorder below 65535 of each of
+ * the n sketches grows by one; each sketch's slot counter grows by one. */
+SSD_API int ssd_advance(ssd_sketch* const* sketches, int n, void* stream);
+
+/* Algorithm 5: global[x] = UnionSE of routers[0..n)[x] for every recorder x,
+ * read as the elementwise minimum (the union of "distance to the nearest slot";
+ * Algorithm 1 prints a maximum, which would keep only recorders every router
+ * saw). All routers must be at the same slot (else SSD_ESTATE); the global
+ * sketch takes that slot. `global` must not be one of the routers. */
+SSD_API int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, void* stream);
+
+/* Regain the sliding super points of a (global) sketch (Sec. 3.3, Sec. 4.2):
+ * hot estimators (R_k >= threshold, R_k = recorders below k), candidate tuples
+ * row by row with the overlap test between B(i-1) and B(i), B(j) = he_0 XOR
+ * he_j (Algorithms 6-7), and the final test R_k(UnionSE of the tuple) >=
+ * threshold with UnionSE the elementwise maximum (Algorithm 1), after which the
+ * host is the 32-bit value whose q-bit windows are B(1..r-1) (a tuple naming a
+ * bit beyond bit 31 yields none). The list is ascending and duplicate-free; a
+ * host regained from several tuples gets the largest R_k.
+ * Writes up to `cap` hosts to d_ips and their R_k to d_rk (device) and the list
+ * size to *n_out (host). Waits for `stream`. Returns SSD_ECAPACITY when the
+ * list is longer than cap (*n_out = the full size, nothing written) or when an
+ * internal capacity overflowed (see ssd_stats_get). */
+SSD_API int ssd_regain(ssd_ctx* ctx, const ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap,
+               uint64_t* n_out, void* stream);
+
+/* End of slot for n routers, fully asynchronous and free of host
+ * synchronisation (it can be captured in a CUDA graph): one streaming pass
+ * merges the routers (Algorithm 5, min reading), writes the merged RSEA to
+ * `global` when it is not NULL, finds the hot estimators of the merged RSEA and
+ * then advances every router's recorders (Sec. 4.3); the candidate levels, final
+ * test and list follow as in ssd_regain. The list size goes to *d_n_out (device
+ * uint64); the list itself to d_ips/d_rk when it fits `cap`. Status and
+ * counters are read afterwards with ssd_stats_get. Routers must share one slot
+ * (SSD_ESTATE); each advances by one slot, `global` takes the merged slot. */
+SSD_API int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* global, uint32_t* d_ips,
+                   uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out, void* stream);
+
+/* Tracing: when set, ssd_close_slot and ssd_regain record ev_start just before
+ * their streaming pass, ev_pass after the streaming pass (merge / hot extraction
+ * / advance) and ev_end after the list is written, on their stream. The events
+ * are cudaEvent_t passed as void*, created by the caller; NULLs switch tracing
+ * off. */
+SSD_API int ssd_set_trace(ssd_ctx* ctx, void* ev_start, void* ev_pass, void* ev_end);
+
+/* Counters of the context's last regain or close (waits for `stream`). */
+SSD_API int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream);
+
+/* Kernels this context has launched so far. */
+SSD_API uint64_t ssd_launch_count(const ssd_ctx* ctx);
+
+/* Message for an SSD_E* code (static storage). */
+SSD_API const char* ssd_strerror(int code);
+/* The last CUDA error seen by this thread inside the library, or "". */
+SSD_API const char* ssd_last_cuda_error(void);
+/* ABI version, major * 100 + minor. */
+SSD_API int ssd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSD_H */

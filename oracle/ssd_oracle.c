@@ -53,9 +53,12 @@ typedef struct orc_params {
 
 /* ------------------------------------------------------------------ checks */
 
+ORC_API int orc_threshold(uint32_t eta, uint32_t theta, uint32_t* thr, double* rhat);
+
 /* Parameter constraints stated in the paper: delta < q and (r-2)*delta + q >= 32
  * (Eq. 2-3), k < 65535 (Sec. 3.2: a distance recorder is an unsigned short).
- * log2_eta and q are bounded so the arrays stay addressable. */
+ * log2_eta and q are bounded so the arrays stay addressable, and the threshold
+ * must round robustly (R7). */
 ORC_API int orc_check_params(const orc_params* p) {
   if (p->r < 3 || p->r > ORC_MAX_R) return -1;
   if (p->delta == 0 || p->delta >= p->q || p->q > 24) return -1;
@@ -63,6 +66,8 @@ ORC_API int orc_check_params(const orc_params* p) {
   if (p->log2_eta < 1 || p->log2_eta > 15) return -1;
   if (p->k < 1 || p->k > 65534) return -1;
   if (p->theta < 1) return -1;
+  uint32_t thr;
+  if (orc_threshold(1u << p->log2_eta, p->theta, &thr, NULL)) return -1;
   return 0;
 }
 

@@ -1,0 +1,272 @@
+"""GB300 sliding super point detector (arXiv 1803.11036), Python binding.
+
+Every step runs in the CUDA library behind ``include/ssd.h``; this module only
+marshals arguments. PyTorch provides device memory (pair buffers and list
+outputs are CUDA tensors) and streams. Names follow the paper: a router's
+sketch is its RSEA, ``scan`` is Algorithm 2, ``advance`` the distance recorder
+update, ``merge`` Algorithm 5, ``regain`` the reconstruction of sliding super
+points, ``close_slot`` all end-of-slot work fused.
+
+Typical slot loop on n routers::
+
+    ctx = Context(params, tables)          # tables: 2048 uint32 (H1 then RHFG[0])
+    routers = [ctx.sketch() for _ in range(n)]
+    for each slot:
+        ctx.scan_batch(routers, pair_tensors)          # or ctx.scan per router
+        ips, rk = ctx.close_slot(routers)               # merge + regain + advance
+"""
+from __future__ import annotations
+
+import ctypes
+import weakref
+
+import numpy as np
+
+from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_STATUS_CTB_OVERFLOW,  # noqa: F401
+                   SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
+                   Params, SSDError, Stats, check, load)
+
+__all__ = ["Context", "Sketch", "SSDError", "SSD_VERIFY_H0", "SSD_NO_PRUNE", "make_params", "threshold",
+           "params_ok", "library_path"]
+
+
+def library_path() -> str:
+    from . import _abi
+    return _abi.lib_path()
+
+
+def make_params(d: dict, flags: int = 0, hse_capacity: int = 0, ctb_capacity: int = 0,
+                out_capacity: int = 0) -> Params:
+    """Params from a dict with log2_eta, q, r, delta, k, theta (and optional flags)."""
+    return Params(d["log2_eta"], d["q"], d["r"], d["delta"], d["k"], d["theta"], d.get("flags", 0) | flags,
+                  hse_capacity, ctb_capacity, out_capacity)
+
+
+def params_ok(p: Params) -> bool:
+    return load().ssd_params_check(ctypes.byref(p)) == 0
+
+
+def threshold(p: Params) -> int:
+    thr = ctypes.c_uint32()
+    check(load().ssd_threshold(ctypes.byref(p), ctypes.byref(thr)), "ssd_threshold")
+    return thr.value
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream, device) -> ctypes.c_void_p:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _pairs_ptr(t, device):
+    """Device pointer and packet count of a pair tensor: 4-byte integers, (n, 2) or (2n,), contiguous."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("pairs must be a CUDA tensor")
+    if t.device != device:
+        raise ValueError(f"pairs on {t.device}, context on {device}")
+    if t.element_size() != 4 or not t.is_contiguous():
+        raise ValueError("pairs must be a contiguous tensor of 4-byte integers")
+    n = t.numel()
+    if n % 2:
+        raise ValueError("pairs hold (cip, oip) couples: even element count")
+    return ctypes.c_void_p(t.data_ptr() if n else 0), n // 2
+
+
+class Sketch:
+    """One RSEA on the device (a router's or the global one)."""
+
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        check(ctx.L.ssd_sketch_create(ctx._h, ctypes.byref(self._h)), "ssd_sketch_create")
+        ctx._sketches.add(self)
+
+    @property
+    def slot(self) -> int:
+        v = ctypes.c_uint64()
+        check(self.ctx.L.ssd_sketch_slot(self._h, ctypes.byref(v)), "ssd_sketch_slot")
+        return v.value
+
+    def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
+        """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""
+        n = self.ctx.sketch_bytes // 2
+        count = n - first if count is None else count
+        out = np.empty(count, dtype=np.uint16)
+        check(self.ctx.L.ssd_sketch_export(self._h, first, count, out.ctypes.data,
+                                           _stream_handle(stream, self.ctx.device)), "ssd_sketch_export")
+        return out
+
+    def export_estimator(self, row: int, col: int, stream=None) -> np.ndarray:
+        eta = 1 << self.ctx.params.log2_eta
+        return self.export(((row << self.ctx.params.q) + col) * eta, eta, stream)
+
+    def load(self, recorders: np.ndarray, slot: int, stream=None) -> None:
+        """Overwrite every recorder from a host uint16 array and set the slot counter."""
+        a = np.ascontiguousarray(recorders, dtype=np.uint16)
+        if a.nbytes != self.ctx.sketch_bytes:
+            raise ValueError("recorder array has the wrong size")
+        check(self.ctx.L.ssd_sketch_import(self._h, a.ctypes.data, slot,
+                                           _stream_handle(stream, self.ctx.device)), "ssd_sketch_import")
+
+    def close(self) -> None:
+        if self._h:
+            self.ctx.L.ssd_sketch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _handles(sketches):
+    arr = (ctypes.c_void_p * len(sketches))(*[s._h.value for s in sketches])
+    return arr
+
+
+class Context:
+    """Detector parameters, hash tables and scratch on one CUDA device."""
+
+    def __init__(self, params, tables, device: int = 0):
+        self.L = load()
+        self.params = params if isinstance(params, Params) else make_params(params)
+        tab = np.ascontiguousarray(tables, dtype=np.uint32)
+        if tab.size != 2048:
+            raise ValueError("tables must hold 2048 uint32 words")
+        torch = _torch()
+        self.device = torch.device("cuda", device)
+        self._h = ctypes.c_void_p()
+        self._sketches = weakref.WeakSet()
+        check(self.L.ssd_create(ctypes.byref(self.params), tab.ctypes.data, device, ctypes.byref(self._h)),
+              "ssd_create")
+        self.sketch_bytes = int(self.L.ssd_sketch_bytes(self._h))
+        self.threshold = threshold(self.params)
+        self._n_out = torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    def sketch(self) -> Sketch:
+        return Sketch(self)
+
+    # -- Algorithm 2 --
+    def scan(self, sketch: Sketch, pairs, stream=None) -> None:
+        ptr, n = _pairs_ptr(pairs, self.device)
+        check(self.L.ssd_scan(sketch._h, ptr, n, _stream_handle(stream, self.device)), "ssd_scan")
+
+    def scan_host(self, sketch: Sketch, pairs, stream=None) -> None:
+        """Algorithm 2 on pairs in host memory: a (n, 2) uint32 numpy array or a CPU tensor
+        (pinned for overlap). With pinned memory keep the buffer unchanged until the stream
+        has passed this call."""
+        torch = _torch()
+        if isinstance(pairs, torch.Tensor):
+            if pairs.is_cuda or pairs.element_size() != 4 or not pairs.is_contiguous():
+                raise ValueError("host pairs: contiguous CPU tensor of 4-byte integers")
+            ptr, n = pairs.data_ptr(), pairs.numel() // 2
+        else:
+            a = np.ascontiguousarray(pairs, dtype=np.uint32)
+            ptr, n = a.ctypes.data, a.size // 2
+            self._host_keep = a
+        check(self.L.ssd_scan_host(sketch._h, ctypes.c_void_p(ptr), n, _stream_handle(stream, self.device)),
+              "ssd_scan_host")
+
+    def set_trace(self, ev_start=None, ev_pass=None, ev_end=None) -> None:
+        """torch.cuda.Event objects recorded at the start, after the streaming pass and at the
+        end of each close_slot / regain; all None switches tracing off."""
+        h = [ctypes.c_void_p(e.cuda_event) if e is not None else None for e in (ev_start, ev_pass, ev_end)]
+        check(self.L.ssd_set_trace(self._h, *h), "ssd_set_trace")
+
+    def scan_batch(self, sketches, pairs_list, stream=None) -> None:
+        if len(sketches) != len(pairs_list):
+            raise ValueError("one pair tensor per sketch")
+        ptrs, counts = [], []
+        for t in pairs_list:
+            p, n = _pairs_ptr(t, self.device)
+            ptrs.append(p.value or 0)
+            counts.append(n)
+        P = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        N = (ctypes.c_uint64 * len(counts))(*counts)
+        check(self.L.ssd_scan_batch(_handles(sketches), P, N, len(sketches), _stream_handle(stream, self.device)),
+              "ssd_scan_batch")
+
+    # -- Sec. 4.3 --
+    def advance(self, sketches, stream=None) -> None:
+        check(self.L.ssd_advance(_handles(sketches), len(sketches), _stream_handle(stream, self.device)),
+              "ssd_advance")
+
+    # -- Algorithm 5 --
+    def merge(self, routers, global_sketch: Sketch, stream=None) -> None:
+        check(self.L.ssd_merge(_handles(routers), len(routers), global_sketch._h,
+                               _stream_handle(stream, self.device)), "ssd_merge")
+
+    def _outputs(self, cap):
+        torch = _torch()
+        return (torch.empty(max(cap, 1), dtype=torch.int32, device=self.device),
+                torch.empty(max(cap, 1), dtype=torch.int32, device=self.device))
+
+    # -- Sec. 3.3 / 4.2 --
+    def regain(self, global_sketch: Sketch, cap: int = 1 << 16, stream=None):
+        """(ips, rk) as int64 CPU tensors of the unsigned values; raises SSDError on overflow."""
+        ips, rk = self._outputs(cap)
+        n = ctypes.c_uint64()
+        rc = self.L.ssd_regain(self._h, global_sketch._h, ctypes.c_void_p(ips.data_ptr()),
+                               ctypes.c_void_p(rk.data_ptr()), cap, ctypes.byref(n),
+                               _stream_handle(stream, self.device))
+        check(rc, "ssd_regain")
+        m = n.value
+        return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
+
+    def close_slot(self, routers, global_sketch: Sketch | None = None, cap: int = 1 << 16, out=None,
+                   stream=None, sync: bool = True):
+        """Merge, regain and advance in one call. With sync=False returns the device
+        tensors (ips, rk, n_out) without waiting; with sync=True returns host arrays."""
+        if out is None:
+            ips, rk = self._outputs(cap)
+            n_out = self._n_out
+        else:
+            ips, rk, n_out = out
+            cap = min(ips.numel(), rk.numel())
+        st = _stream_handle(stream, self.device)
+        check(self.L.ssd_close_slot(self._h, _handles(routers), len(routers),
+                                    global_sketch._h if global_sketch is not None else None,
+                                    ctypes.c_void_p(ips.data_ptr()), ctypes.c_void_p(rk.data_ptr()), cap,
+                                    ctypes.c_void_p(n_out.data_ptr()), st), "ssd_close_slot")
+        if not sync:
+            return ips, rk, n_out
+        s = self.stats(stream)
+        if s["status"]:
+            raise SSDError(SSD_ECAPACITY, f"ssd_close_slot (status {s['status']})")
+        m = int(n_out.item())
+        return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
+
+    def stats(self, stream=None) -> dict:
+        st = Stats()
+        check(self.L.ssd_stats_get(self._h, ctypes.byref(st), _stream_handle(stream, self.device)),
+              "ssd_stats_get")
+        r = self.params.r
+        return dict(status=st.status, threshold=st.threshold, hot=list(st.hot)[:r], level=list(st.level)[:r],
+                    raw=st.raw, n_out=st.n_out)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.L.ssd_launch_count(self._h))
+
+    def close(self) -> None:
+        if self._h:
+            for sk in list(self._sketches):
+                sk.close()
+            self.L.ssd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

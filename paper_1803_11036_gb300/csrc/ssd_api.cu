@@ -1,0 +1,524 @@
+// The C ABI of include/ssd.h: parameter checks, contexts, sketches and the
+// launch sequences of scan, advance, merge, regain and slot close.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ssd_internal.cuh"
+
+struct ssd_ctx {
+  ssd_params p;
+  int device;
+  int sms;
+  ssd::Dims d;
+  ssd::Scratch s;
+  uint32_t* tables;
+  uint32_t* hot_idx;
+  uint32_t* pool_col;
+  uint32_t* pool_rk;
+  uint32_t* pool_bm;
+  uint32_t* ctb[2];
+  unsigned long long* stage;
+  ssd::DevCounters* counters;
+  unsigned long long* n_out;  // list size of ssd_regain
+  uint64_t launches;
+  // tracing events (caller-owned)
+  cudaEvent_t tr_start, tr_pass, tr_end;
+  // host-pair staging of ssd_scan_host
+  uint32_t* stage_pairs[2];
+  uint64_t stage_alpha;
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_copied[2], ev_scanned[2];
+};
+
+struct ssd_sketch {
+  ssd_ctx* ctx;
+  int device;
+  uint16_t* dr;
+  uint64_t slot;
+};
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+  return SSD_ECUDA;
+}
+
+#define SSD_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Makes ctx's device current for the duration of a call and restores the caller's.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) == cudaSuccess && prev_ != dev) changed_ = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = -1;
+  bool changed_ = false;
+};
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+int threshold_of(uint32_t eta, uint32_t theta, uint32_t* thr) {
+  // Sec. 3.3: an estimator is hot when R_k >= eta * (1 - e^(-theta/eta)).
+  const double e = (double)eta;
+  const double v = e * (1.0 - std::exp(-(double)theta / e));
+  if (std::fabs(v - std::nearbyint(v)) < 1e-9) return SSD_EINVAL;
+  *thr = (uint32_t)std::ceil(v);
+  return SSD_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool same_ctx(ssd_sketch* const* v, int n, ssd_ctx** ctx) {
+  if (!v || n < 1 || n > SSD_MAX_ROUTERS || !v[0]) return false;
+  *ctx = v[0]->ctx;
+  for (int i = 0; i < n; ++i)
+    if (!v[i] || v[i]->ctx != *ctx) return false;
+  return true;
+}
+
+int add_job(ssd::ScanBatch& b, int j, uint16_t* dr, const uint32_t* pairs, uint64_t n, uint64_t* prefix) {
+  if (n && !pairs) return SSD_EINVAL;
+  if (reinterpret_cast<uintptr_t>(pairs) & 7u) return SSD_EINVAL;
+  const uint32_t* head = nullptr;
+  const uint32_t* body = pairs;
+  uint64_t rest = n;
+  if (n && (reinterpret_cast<uintptr_t>(pairs) & 15u)) {  // starts at 8 mod 16
+    head = pairs;
+    body = pairs + 2;
+    rest = n - 1;
+  }
+  b.dr[j] = dr;
+  b.vec[j] = reinterpret_cast<const uint4*>(body);
+  b.edge[2 * j] = head;
+  b.edge[2 * j + 1] = (rest & 1u) ? body + 2 * (rest - 1) : nullptr;
+  b.prefix[j] = *prefix;
+  *prefix += rest / 2;
+  return SSD_OK;
+}
+
+int scan_jobs(ssd_ctx* ctx, ssd::ScanBatch& b, uint64_t total_vec, bool any_edge, cudaStream_t st) {
+  if (total_vec == 0 && !any_edge) return SSD_OK;
+  uint64_t grid = (total_vec + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
+  const uint64_t cap = (uint64_t)ctx->sms * 8;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  cudaError_t e = ssd::launch_scan(ctx->d, ctx->tables, b, (int)grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "scan kernel");
+  ctx->launches += 1;
+  return SSD_OK;
+}
+
+int stream_pass(ssd_ctx* ctx, ssd_sketch* const* routers, int n, uint16_t* global, int mode, cudaStream_t st) {
+  ssd::StreamArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  for (int i = 0; i < n; ++i) a.routers[i] = routers[i]->dr;
+  a.global = global;
+  cudaError_t e = ssd::launch_stream(ctx->d, ctx->s, a, mode, ctx->sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream kernel");
+  ctx->launches += 1;
+  return SSD_OK;
+}
+
+int trace(ssd_ctx* ctx, cudaEvent_t ev, cudaStream_t st) {
+  if (!ev) return SSD_OK;
+  cudaError_t e = cudaEventRecord(ev, st);
+  return e == cudaSuccess ? SSD_OK : cuda_fail(e, "cudaEventRecord (trace)");
+}
+
+int regain_after_pass(ssd_ctx* ctx, uint32_t* ips, uint32_t* rk, uint64_t cap, unsigned long long* n_out,
+                      cudaStream_t st) {
+  int launches = 0;
+  cudaError_t e = ssd::launch_regain_tail(ctx->d, ctx->s, ips, rk, cap, n_out, ctx->sms, st, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(e, "regain kernels");
+  return SSD_OK;
+}
+
+void free_ctx(ssd_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    if (c->ev_scanned[i]) cudaEventDestroy(c->ev_scanned[i]);
+    cudaFree(c->stage_pairs[i]);
+  }
+  cudaFree(c->tables);
+  cudaFree(c->hot_idx);
+  cudaFree(c->pool_col);
+  cudaFree(c->pool_rk);
+  cudaFree(c->pool_bm);
+  cudaFree(c->ctb[0]);
+  cudaFree(c->ctb[1]);
+  cudaFree(c->stage);
+  cudaFree(c->counters);
+  cudaFree(c->n_out);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssd_version(void) { return 100; }
+
+const char* ssd_strerror(int code) {
+  switch (code) {
+    case SSD_OK: return "ok";
+    case SSD_EINVAL: return "invalid argument or parameter set";
+    case SSD_ENOMEM: return "device memory allocation failed";
+    case SSD_ECAPACITY: return "a capacity was exceeded";
+    case SSD_ECUDA: return "CUDA error";
+    case SSD_ETIMEOUT: return "device-side wait timed out";
+    case SSD_ESTATE: return "sketches disagree on their slot or context";
+    default: return "unknown error";
+  }
+}
+
+const char* ssd_last_cuda_error(void) { return g_cuda_err; }
+
+int ssd_params_check(const ssd_params* p) {
+  if (!p) return SSD_EINVAL;
+  if (p->log2_eta < 5 || p->log2_eta > 15) return SSD_EINVAL;
+  if (p->r < 3 || p->r > SSD_MAX_R) return SSD_EINVAL;
+  if (p->delta == 0 || p->delta >= p->q || p->q > 24) return SSD_EINVAL;
+  if ((p->r - 2) * p->delta + p->q < 32) return SSD_EINVAL;  // Eq. 2-3: every bit of cip in some B(i)
+  if (p->k < 1 || p->k > 65534) return SSD_EINVAL;            // Sec. 3.2: k < 65535
+  if (p->theta < 1) return SSD_EINVAL;
+  if (p->flags & ~(SSD_VERIFY_H0 | SSD_NO_PRUNE)) return SSD_EINVAL;
+  if (p->ctb_capacity > (1ull << 32) || p->out_capacity > (1ull << 28)) return SSD_EINVAL;
+  uint32_t thr;
+  return threshold_of(1u << p->log2_eta, p->theta, &thr);
+}
+
+int ssd_threshold(const ssd_params* p, uint32_t* thr) {
+  if (!p || !thr) return SSD_EINVAL;
+  return threshold_of(1u << p->log2_eta, p->theta, thr);
+}
+
+int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx** out) {
+  if (!out) return SSD_EINVAL;
+  *out = nullptr;
+  if (!tables || ssd_params_check(p) != SSD_OK) return SSD_EINVAL;
+  int ndev = 0;
+  SSD_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return SSD_EINVAL;
+  DeviceGuard g(device);
+  ssd_ctx* c = new (std::nothrow) ssd_ctx;
+  if (!c) return SSD_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->p = *p;
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "cudaDeviceGetAttribute"); }
+
+  ssd::Dims& d = c->d;
+  d.log2_eta = p->log2_eta; d.q = p->q; d.r = p->r; d.delta = p->delta; d.k = p->k; d.flags = p->flags;
+  threshold_of(1u << p->log2_eta, p->theta, &d.thr);
+  d.eta = 1u << p->log2_eta;
+  d.words = d.eta / 32;
+  d.col_mask = (1u << p->q) - 1u;
+  d.low_bits = p->q - p->delta;
+  d.low_mask = (1u << d.low_bits) - 1u;
+  const uint64_t C = 1ull << p->q;
+  d.hse_cap = p->hse_capacity ? p->hse_capacity : (uint32_t)(C < 65536 ? C : 65536);
+  if (d.hse_cap > C) d.hse_cap = (uint32_t)C;
+  d.ctb_cap = p->ctb_capacity ? p->ctb_capacity : (1ull << 22);
+  d.out_cap = pow2_at_least(p->out_capacity ? p->out_capacity : (1ull << 20));
+
+  const uint64_t R = p->r;
+  struct Alloc { void** ptr; uint64_t bytes; } allocs[] = {
+      {(void**)&c->tables, 2048 * 4},
+      {(void**)&c->hot_idx, R * C * 4},
+      {(void**)&c->pool_col, R * d.hse_cap * 4},
+      {(void**)&c->pool_rk, R * d.hse_cap * 4},
+      {(void**)&c->pool_bm, R * d.hse_cap * (uint64_t)d.words * 4},
+      {(void**)&c->ctb[0], d.ctb_cap * R * 4},
+      {(void**)&c->ctb[1], d.ctb_cap * R * 4},
+      {(void**)&c->stage, d.out_cap * 8},
+      {(void**)&c->counters, sizeof(ssd::DevCounters)},
+      {(void**)&c->n_out, 8},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_ctx(c);
+      return SSD_ENOMEM;
+    }
+  }
+  e = cudaMemcpy(c->tables, tables, 2048 * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(ssd::DevCounters));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "ssd_create"); }
+  c->s.tables = c->tables;
+  c->s.hot_idx = c->hot_idx;
+  c->s.pool_col = c->pool_col;
+  c->s.pool_rk = c->pool_rk;
+  c->s.pool_bm = c->pool_bm;
+  c->s.ctb[0] = c->ctb[0];
+  c->s.ctb[1] = c->ctb[1];
+  c->s.stage = c->stage;
+  c->s.counters = c->counters;
+  *out = c;
+  return SSD_OK;
+}
+
+void ssd_destroy(ssd_ctx* ctx) { free_ctx(ctx); }
+
+uint64_t ssd_sketch_bytes(const ssd_ctx* ctx) {
+  if (!ctx) return 0;
+  return (uint64_t)ctx->p.r << (ctx->p.q + ctx->p.log2_eta + 1);
+}
+
+int ssd_sketch_create(ssd_ctx* ctx, ssd_sketch** out) {
+  if (!ctx || !out) return SSD_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  ssd_sketch* s = new (std::nothrow) ssd_sketch;
+  if (!s) return SSD_ENOMEM;
+  s->ctx = ctx;
+  s->device = ctx->device;
+  s->slot = 0;
+  s->dr = nullptr;
+  const uint64_t bytes = ssd_sketch_bytes(ctx);
+  if (cudaMalloc(&s->dr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return SSD_ENOMEM;
+  }
+  // every distance recorder starts at 65535 (Sec. 3.2)
+  cudaError_t e = cudaMemsetAsync(s->dr, 0xFF, bytes, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    cudaFree(s->dr);
+    delete s;
+    return cuda_fail(e, "ssd_sketch_create");
+  }
+  *out = s;
+  return SSD_OK;
+}
+
+void ssd_sketch_destroy(ssd_sketch* s) {
+  if (!s) return;
+  DeviceGuard g(s->device);
+  cudaFree(s->dr);
+  delete s;
+}
+
+int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot) {
+  if (!s || !slot) return SSD_EINVAL;
+  *slot = s->slot;
+  return SSD_OK;
+}
+
+int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
+  if (!s || (count && !dst)) return SSD_EINVAL;
+  const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;
+  if (first > n || count > n - first) return SSD_EINVAL;
+  if (!count) return SSD_OK;
+  DeviceGuard g(s->ctx->device);
+  SSD_CUDA(cudaMemcpyAsync(dst, s->dr + first, count * 2, cudaMemcpyDefault, as_stream(stream)));
+  SSD_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  return SSD_OK;
+}
+
+int ssd_sketch_import(ssd_sketch* s, const uint16_t* src, uint64_t slot, void* stream) {
+  if (!s || !src) return SSD_EINVAL;
+  DeviceGuard g(s->ctx->device);
+  SSD_CUDA(cudaMemcpyAsync(s->dr, src, ssd_sketch_bytes(s->ctx), cudaMemcpyDefault, as_stream(stream)));
+  SSD_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  s->slot = slot;
+  return SSD_OK;
+}
+
+int ssd_scan(ssd_sketch* s, const uint32_t* d_pairs, uint64_t n_pairs, void* stream) {
+  if (!s) return SSD_EINVAL;
+  return ssd_scan_batch(&s, &d_pairs, &n_pairs, 1, stream);
+}
+
+int ssd_scan_batch(ssd_sketch* const* sketches, const uint32_t* const* d_pairs, const uint64_t* n_pairs, int n,
+                   void* stream) {
+  ssd_ctx* ctx = nullptr;
+  if (!same_ctx(sketches, n, &ctx) || !d_pairs || !n_pairs) return SSD_EINVAL;
+  ssd::ScanBatch b;
+  std::memset(&b, 0, sizeof(b));
+  b.n = n;
+  uint64_t prefix = 0;
+  bool any_edge = false;
+  for (int j = 0; j < n; ++j) {
+    int rc = add_job(b, j, sketches[j]->dr, d_pairs[j], n_pairs[j], &prefix);
+    if (rc != SSD_OK) return rc;
+    any_edge = any_edge || b.edge[2 * j] || b.edge[2 * j + 1];
+  }
+  b.prefix[n] = prefix;
+  DeviceGuard g(ctx->device);
+  return scan_jobs(ctx, b, prefix, any_edge, as_stream(stream));
+}
+
+int ssd_scan_host(ssd_sketch* s, const uint32_t* h_pairs, uint64_t n_pairs, void* stream) {
+  if (!s || (n_pairs && !h_pairs)) return SSD_EINVAL;
+  if (n_pairs == 0) return SSD_OK;
+  ssd_ctx* ctx = s->ctx;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  if (!ctx->copy_stream) {  // first call: the two alpha-pair device buffers of Sec. 4.1
+    const uint64_t alpha = 1ull << 22;
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&ctx->stage_pairs[i], alpha * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return SSD_ENOMEM;
+      }
+      SSD_CUDA(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming));
+      SSD_CUDA(cudaEventCreateWithFlags(&ctx->ev_scanned[i], cudaEventDisableTiming));
+    }
+    SSD_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    ctx->stage_alpha = alpha;
+  }
+  // the copy stream starts after whatever the caller queued before this call
+  SSD_CUDA(cudaEventRecord(ctx->ev_scanned[0], st));
+  SSD_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_scanned[0], 0));
+  uint64_t done = 0;
+  for (int c = 0; done < n_pairs; ++c) {
+    const int b = c & 1;
+    const uint64_t m = n_pairs - done < ctx->stage_alpha ? n_pairs - done : ctx->stage_alpha;
+    if (c >= 2) SSD_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_scanned[b], 0));  // buffer b is free
+    SSD_CUDA(cudaMemcpyAsync(ctx->stage_pairs[b], h_pairs + 2 * done, m * 8, cudaMemcpyHostToDevice,
+                             ctx->copy_stream));
+    SSD_CUDA(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    SSD_CUDA(cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+    const uint32_t* dp = ctx->stage_pairs[b];
+    int rc = ssd_scan_batch(&s, &dp, &m, 1, stream);
+    if (rc != SSD_OK) return rc;
+    SSD_CUDA(cudaEventRecord(ctx->ev_scanned[b], st));
+    done += m;
+  }
+  return SSD_OK;
+}
+
+int ssd_set_trace(ssd_ctx* ctx, void* ev_start, void* ev_pass, void* ev_end) {
+  if (!ctx) return SSD_EINVAL;
+  ctx->tr_start = reinterpret_cast<cudaEvent_t>(ev_start);
+  ctx->tr_pass = reinterpret_cast<cudaEvent_t>(ev_pass);
+  ctx->tr_end = reinterpret_cast<cudaEvent_t>(ev_end);
+  return SSD_OK;
+}
+
+int ssd_advance(ssd_sketch* const* sketches, int n, void* stream) {
+  ssd_ctx* ctx = nullptr;
+  if (!same_ctx(sketches, n, &ctx)) return SSD_EINVAL;
+  DeviceGuard g(ctx->device);
+  int rc = stream_pass(ctx, sketches, n, nullptr, ssd::kAdvance, as_stream(stream));
+  if (rc != SSD_OK) return rc;
+  for (int i = 0; i < n; ++i) sketches[i]->slot += 1;
+  return SSD_OK;
+}
+
+int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, void* stream) {
+  ssd_ctx* ctx = nullptr;
+  if (!same_ctx(routers, n, &ctx) || !global || global->ctx != ctx) return SSD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (routers[i] == global) return SSD_EINVAL;
+    if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
+  }
+  DeviceGuard g(ctx->device);
+  int rc = stream_pass(ctx, routers, n, global->dr, 0, as_stream(stream));
+  if (rc != SSD_OK) return rc;
+  global->slot = routers[0]->slot;
+  return SSD_OK;
+}
+
+int ssd_regain(ssd_ctx* ctx, const ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap,
+               uint64_t* n_out, void* stream) {
+  if (!ctx || !global || global->ctx != ctx || !n_out || (cap && (!d_ips || !d_rk))) return SSD_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
+  int rc = trace(ctx, ctx->tr_start, st);
+  if (rc != SSD_OK) return rc;
+  ssd_sketch* one = const_cast<ssd_sketch*>(global);
+  rc = stream_pass(ctx, &one, 1, nullptr, ssd::kHot, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_pass, st);
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, ctx->n_out, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
+  if (rc != SSD_OK) return rc;
+  ssd::DevCounters h;
+  SSD_CUDA(cudaMemcpyAsync(&h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SSD_CUDA(cudaStreamSynchronize(st));
+  *n_out = h.n_out;
+  if (h.status & (SSD_STATUS_HSE_OVERFLOW | SSD_STATUS_CTB_OVERFLOW | SSD_STATUS_OUT_OVERFLOW |
+                  SSD_STATUS_LIST_OVERFLOW))
+    return SSD_ECAPACITY;
+  return SSD_OK;
+}
+
+int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* global, uint32_t* d_ips,
+                   uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out, void* stream) {
+  ssd_ctx* c2 = nullptr;
+  if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx) return SSD_EINVAL;
+  if (global && global->ctx != ctx) return SSD_EINVAL;
+  if (cap && (!d_ips || !d_rk)) return SSD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (routers[i] == global) return SSD_EINVAL;
+    if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
+  int rc = trace(ctx, ctx->tr_start, st);
+  if (rc != SSD_OK) return rc;
+  rc = stream_pass(ctx, routers, n, global ? global->dr : nullptr, ssd::kAdvance | ssd::kHot, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_pass, st);
+  unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
+  if (rc != SSD_OK) return rc;
+  const uint64_t merged = routers[0]->slot;
+  for (int i = 0; i < n; ++i) routers[i]->slot += 1;
+  if (global) global->slot = merged;
+  return SSD_OK;
+}
+
+int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
+  if (!ctx || !out) return SSD_EINVAL;
+  DeviceGuard g(ctx->device);
+  ssd::DevCounters h;
+  SSD_CUDA(cudaMemcpyAsync(&h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost, as_stream(stream)));
+  SSD_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  std::memset(out, 0, sizeof(*out));
+  out->status = h.status;
+  out->threshold = ctx->d.thr;
+  for (uint32_t i = 0; i < SSD_MAX_R; ++i) {
+    out->hot[i] = i < ctx->d.r ? h.hot[i] : 0;
+    out->level[i] = i < ctx->d.r ? h.level[i] : 0;
+  }
+  out->level[0] = out->hot[0];
+  out->raw = h.raw;
+  out->n_out = h.n_out;
+  return SSD_OK;
+}
+
+uint64_t ssd_launch_count(const ssd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of the detector.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssd.h"
+
+namespace ssd {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;  // "not hot" in the per-estimator pool index
+constexpr int kBlock = 256;
+
+// Device counters of one regain / slot close (zeroed before each).
+struct DevCounters {
+  unsigned int hot[SSD_MAX_R];              // true |HSE(i)|
+  unsigned int status;                      // SSD_STATUS_* bits
+  unsigned int pad_;
+  unsigned long long level[SSD_MAX_R];      // candidates covering rows 0..i
+  unsigned long long raw;                   // accepted full tuples (staged)
+  unsigned long long n_out;                 // unique hosts
+};
+
+// Dimensions and derived constants, passed by value.
+struct Dims {
+  uint32_t log2_eta, q, r, delta, k, thr, flags;
+  uint32_t eta;        // 2^log2_eta
+  uint32_t words;      // eta / 32: bitmap words per estimator
+  uint32_t col_mask;   // 2^q - 1
+  uint32_t low_bits;   // q - delta
+  uint32_t low_mask;   // 2^(q-delta) - 1
+  uint32_t hse_cap;    // pool entries per row
+  uint64_t ctb_cap;    // tuples per candidate buffer
+  uint64_t out_cap;    // staged accepted tuples (a power of two)
+};
+
+// Scratch of a context (all device memory).
+struct Scratch {
+  const uint32_t* tables;   // 2048 words: H1 tables then RHFG[0] tables
+  uint32_t* hot_idx;        // [r][2^q] pool index of a hot estimator, kNone otherwise
+  uint32_t* pool_col;       // [r][hse_cap] column of each pooled hot estimator
+  uint32_t* pool_rk;        // [r][hse_cap] its R_k
+  uint32_t* pool_bm;        // [r][hse_cap][words] bit j = (recorder j < k)
+  uint32_t* ctb[2];         // candidate tuple buffers, tuple stride r (pool indices)
+  unsigned long long* stage;  // [out_cap] (cip << 32) | R_k of accepted tuples
+  DevCounters* counters;
+};
+
+// ---- scan (ssd_scan.cu) ----
+constexpr int kMaxBatch = SSD_MAX_ROUTERS;
+struct ScanJob {
+  uint16_t* dr;              // the router's recorders
+  const uint4* vec;          // 16-byte aligned start of its vector body
+  uint64_t nvec;             // packets / 2 in the body
+  const uint32_t* head;      // a leading packet outside the body, or nullptr
+  const uint32_t* tail;      // a trailing packet outside the body, or nullptr
+};
+struct ScanBatch {
+  int n;
+  uint64_t prefix[kMaxBatch + 1];  // prefix sums of nvec
+  uint16_t* dr[kMaxBatch];
+  const uint4* vec[kMaxBatch];
+  const uint32_t* edge[2 * kMaxBatch];  // head, tail per router (nullptr when absent)
+};
+cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, cudaStream_t st);
+
+// ---- streaming passes (ssd_stream.cu) ----
+struct StreamArgs {
+  int n;                               // routers
+  uint16_t* routers[kMaxBatch];
+  uint16_t* global;                    // merged output, or nullptr
+};
+// mode bits
+constexpr int kAdvance = 1;   // routers += 1 (saturating) after reading
+constexpr int kHot = 2;       // count R_k of the merged value and pool the hot estimators
+cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
+                          cudaStream_t st);
+
+// ---- regain (ssd_regain.cu) ----
+// Candidate levels, final test and the list; reads the pools filled by a kHot pass.
+cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
+                               unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches);
+
+}  // namespace ssd

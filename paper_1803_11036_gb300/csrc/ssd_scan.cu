@@ -1,0 +1,114 @@
+// IP pair scanning (Algorithm 2, Sec. 4.1) for one or many routers in one launch.
+//
+// Each thread takes 16-byte vectors of the pair stream (two packets per
+// vector), hashes both addresses with the simple-tabulation tables held in
+// shared memory, and sets the r recorders RSEA[i, RHFG[i](cip)][H1(oip)] to 0.
+// Setting a recorder to 0 is idempotent and order-free (Sec. 4.1), so the
+// stores need no atomics and no ordering between threads.
+#include "ssd_internal.cuh"
+
+namespace ssd {
+namespace {
+
+__device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
+  return T[x & 255u] ^ T[256u + ((x >> 8) & 255u)] ^ T[512u + ((x >> 16) & 255u)] ^ T[768u + (x >> 24)];
+}
+
+// Algorithm 2 for one pair: DRidx = H1(oip); RHFG[0](cip) from the second table
+// set; RHFG[i](cip) = ((cip >> (i-1)*delta) ^ RHFG[0](cip)) mod 2^q for i >= 1.
+__device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t cip, uint32_t oip,
+                                          const uint32_t* sT, const Dims& d) {
+  const uint32_t j = tab_hash(sT, oip) & (d.eta - 1u);
+  const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
+  dr[((uint64_t)c0 << d.log2_eta) | j] = 0;
+#pragma unroll
+  for (uint32_t i = 1; i < SSD_MAX_R; ++i) {
+    if (i < d.r) {
+      const uint32_t sh = (i - 1u) * d.delta;
+      const uint32_t w = sh < 32u ? (cip >> sh) : 0u;
+      const uint32_t col = (w ^ c0) & d.col_mask;
+      dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = 0;
+    }
+  }
+}
+
+__device__ __forceinline__ int find_router(const ScanBatch& b, uint64_t v) {
+  int lo = 0, hi = b.n - 1;
+  while (lo < hi) {  // last j with prefix[j] <= v
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.prefix[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kUnroll = 4;
+
+__global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* __restrict__ tables,
+                                                 const __grid_constant__ ScanBatch b) {
+  __shared__ uint32_t sT[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
+  __syncthreads();
+
+  // packets outside the 16-byte aligned bodies: a head when a buffer starts at
+  // 8 mod 16, a tail when the body leaves one packet over
+  if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
+    const uint32_t* e = b.edge[threadIdx.x];
+    if (e) scan_pair(b.dr[threadIdx.x >> 1], e[0], e[1], sT, d);
+  }
+
+  const uint64_t total = b.prefix[b.n];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b.n == 1) {
+    const uint4* __restrict__ vec = b.vec[0];
+    uint16_t* __restrict__ dr = b.dr[0];
+    for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
+      uint4 w[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) w[u] = __ldcs(vec + v + u * stride);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        scan_pair(dr, w[u].x, w[u].y, sT, d);
+        scan_pair(dr, w[u].z, w[u].w, sT, d);
+      }
+    }
+    for (; v < total; v += stride) {
+      const uint4 w = __ldcs(vec + v);
+      scan_pair(dr, w.x, w.y, sT, d);
+      scan_pair(dr, w.z, w.w, sT, d);
+    }
+  } else {
+    for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
+      uint4 w[kUnroll];
+      uint16_t* dr[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t vv = v + u * stride;
+        const int j = find_router(b, vv);
+        w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
+        dr[u] = b.dr[j];
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        scan_pair(dr[u], w[u].x, w[u].y, sT, d);
+        scan_pair(dr[u], w[u].z, w[u].w, sT, d);
+      }
+    }
+    for (; v < total; v += stride) {
+      const int j = find_router(b, v);
+      const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
+      scan_pair(b.dr[j], w.x, w.y, sT, d);
+      scan_pair(b.dr[j], w.z, w.w, sT, d);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, cudaStream_t st) {
+  static_assert(sizeof(ScanBatch) < 32000, "kernel parameter block too large");
+  k_scan<<<grid, kBlock, 0, st>>>(d, tables, b);
+  return cudaGetLastError();
+}
+
+}  // namespace ssd

@@ -1,0 +1,235 @@
+// Streaming passes over whole RSEAs: merge (Algorithm 5), hot-estimator
+// extraction (Sec. 3.3) and the distance recorder update (Sec. 4.3).
+//
+// One kernel serves every combination: for each recorder position it reads the
+// n routers' values (16 bytes = 8 recorders per lane), takes their elementwise
+// minimum (the merge), optionally writes that to the global RSEA, optionally
+// counts the merged recorders below k per estimator and pools the hot ones with
+// their "recorder < k" bitmap, and optionally writes every router's value back
+// advanced by one with saturation at 65535. Recorders are read and written once
+// per pass, in 512-byte coalesced warp accesses with streaming cache hints.
+#include "ssd_internal.cuh"
+
+namespace ssd {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// 8 recorders (two per 32-bit word) advanced by one, saturating at 65535: no
+// carry can cross a half because each half is at most 65534 before the add.
+__device__ __forceinline__ uint32_t inc2(uint32_t w) { return __vminu2(w, 0xFFFEFFFEu) + 0x00010001u; }
+__device__ __forceinline__ uint4 inc8(uint4 v) { return make_uint4(inc2(v.x), inc2(v.y), inc2(v.z), inc2(v.w)); }
+__device__ __forceinline__ uint4 min8(uint4 a, uint4 b) {
+  return make_uint4(__vminu2(a.x, b.x), __vminu2(a.y, b.y), __vminu2(a.z, b.z), __vminu2(a.w, b.w));
+}
+// bit i of the result = (recorder i < k) for the 8 recorders of v
+__device__ __forceinline__ uint32_t lt2(uint32_t w, uint32_t kk) {
+  const uint32_t c = __vcmpltu2(w, kk);
+  return (c & 1u) | ((c >> 15) & 2u);
+}
+__device__ __forceinline__ uint32_t lt8(uint4 v, uint32_t kk) {
+  return lt2(v.x, kk) | (lt2(v.y, kk) << 2) | (lt2(v.z, kk) << 4) | (lt2(v.w, kk) << 6);
+}
+
+// Pool a hot estimator: reserve a slot in its row's pool and return it
+// (kNone when the pool is full).
+__device__ __forceinline__ uint32_t pool_slot(const Dims& d, const Scratch& s, uint32_t row) {
+  uint32_t idx = atomicAdd(&s.counters->hot[row], 1u);
+  if (idx >= d.hse_cap) {
+    atomicOr(&s.counters->status, SSD_STATUS_HSE_OVERFLOW);
+    idx = kNone;
+  }
+  return idx;
+}
+
+// eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
+template <bool ONE, bool ADV, bool HOT>
+__global__ void __launch_bounds__(kBlock) k_stream_large(const Dims d, const Scratch s,
+                                                         const __grid_constant__ StreamArgs a) {
+  extern __shared__ __align__(16) uint8_t smask[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* my = smask + (size_t)wid * (d.eta >> 3);
+  const uint64_t n_se = (uint64_t)d.r << d.q;
+  const uint32_t iters = d.eta >> 8;
+  const uint32_t kk = d.k | (d.k << 16);
+  const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  uint4* const g = reinterpret_cast<uint4*>(a.global);
+
+  for (uint64_t se = (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < n_se; se += wstride) {
+    const uint64_t base = (se << d.log2_eta) >> 3;  // in 8-recorder units
+    uint32_t cnt = 0;
+    if (ONE) {
+      uint4* const r0 = reinterpret_cast<uint4*>(a.routers[0]);
+      for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
+        const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < (int)m) v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (u < (int)m) {
+            const uint64_t at = base + (it0 + u) * 32 + lane;
+            if (g) __stcs(g + at, v[u]);
+            if (HOT) {
+              const uint32_t bits = lt8(v[u], kk);
+              cnt += __popc(bits);
+              my[(it0 + u) * 32 + lane] = (uint8_t)bits;
+            }
+            if (ADV) __stcs(r0 + at, inc8(v[u]));
+          }
+        }
+      }
+    } else {
+      for (uint32_t it = 0; it < iters; ++it) {
+        const uint64_t at = base + it * 32 + lane;
+        uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
+        uint4 mv = __ldcs(rp + at);
+        if (ADV) __stcs(rp + at, inc8(mv));
+        for (int n = 1; n < a.n; ++n) {
+          rp = reinterpret_cast<uint4*>(a.routers[n]);
+          const uint4 v = __ldcs(rp + at);
+          mv = min8(mv, v);
+          if (ADV) __stcs(rp + at, inc8(v));
+        }
+        if (g) __stcs(g + at, mv);
+        if (HOT) {
+          const uint32_t bits = lt8(mv, kk);
+          cnt += __popc(bits);
+          my[it * 32 + lane] = (uint8_t)bits;
+        }
+      }
+    }
+    if (HOT) {
+      cnt = __reduce_add_sync(kFull, cnt);
+      const uint32_t row = (uint32_t)(se >> d.q), col = (uint32_t)se & d.col_mask;
+      uint32_t idx = kNone;
+      if (cnt >= d.thr) {  // warp-uniform
+        if (lane == 0) idx = pool_slot(d, s, row);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx != kNone) {
+          __syncwarp();
+          const uint32_t* mw = reinterpret_cast<const uint32_t*>(my);
+          uint32_t* dst = s.pool_bm + ((uint64_t)row * d.hse_cap + idx) * d.words;
+          for (uint32_t w = lane; w < d.words; w += 32) dst[w] = mw[w];
+          if (lane == 0) {
+            s.pool_col[(uint64_t)row * d.hse_cap + idx] = col;
+            s.pool_rk[(uint64_t)row * d.hse_cap + idx] = cnt;
+          }
+        }
+      }
+      if (lane == 0) s.hot_idx[se] = idx;
+      __syncwarp();
+    }
+  }
+}
+
+// 32 <= eta <= 128: L = eta/8 lanes per estimator, 32/L estimators per warp step.
+template <bool ONE, bool ADV, bool HOT>
+__global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scratch s,
+                                                         const __grid_constant__ StreamArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t L = d.eta >> 3;
+  const uint32_t per_warp = 32u / L;
+  const uint64_t n_se = (uint64_t)d.r << d.q;
+  const uint64_t n_units = n_se / per_warp;  // n_se is a multiple of per_warp (2^q >= 2^5)
+  const uint32_t kk = d.k | (d.k << 16);
+  const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  uint4* const g = reinterpret_cast<uint4*>(a.global);
+  uint8_t* const bm_bytes = reinterpret_cast<uint8_t*>(s.pool_bm);
+
+  for (uint64_t u = (uint64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); u < n_units; u += wstride) {
+    const uint64_t at = u * 32 + lane;
+    uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
+    uint4 mv = __ldcs(rp + at);
+    if (ADV) __stcs(rp + at, inc8(mv));
+    if (!ONE) {
+      for (int n = 1; n < a.n; ++n) {
+        rp = reinterpret_cast<uint4*>(a.routers[n]);
+        const uint4 v = __ldcs(rp + at);
+        mv = min8(mv, v);
+        if (ADV) __stcs(rp + at, inc8(v));
+      }
+    }
+    if (g) __stcs(g + at, mv);
+    if (HOT) {
+      const uint32_t bits = lt8(mv, kk);
+      uint32_t cnt = __popc(bits);
+      for (uint32_t o = 1; o < L; o <<= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+      const uint64_t se = u * per_warp + lane / L;
+      const uint32_t row = (uint32_t)(se >> d.q), col = (uint32_t)se & d.col_mask;
+      const uint32_t leader = lane & ~(L - 1);
+      uint32_t idx = kNone;
+      if (lane == leader && cnt >= d.thr) idx = pool_slot(d, s, row);
+      idx = __shfl_sync(kFull, idx, leader);
+      if (idx != kNone) {
+        bm_bytes[((uint64_t)row * d.hse_cap + idx) * (d.eta >> 3) + (lane - leader)] = (uint8_t)bits;
+        if (lane == leader) {
+          s.pool_col[(uint64_t)row * d.hse_cap + idx] = col;
+          s.pool_rk[(uint64_t)row * d.hse_cap + idx] = cnt;
+        }
+      }
+      if (lane == leader) s.hot_idx[se] = idx;
+    }
+  }
+}
+
+template <bool ONE, bool ADV, bool HOT>
+cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a, int sms, cudaStream_t st) {
+  if (d.eta >= 256) {
+    const size_t smem = HOT ? (size_t)(kBlock / 32) * (d.eta >> 3) : 0;
+    static int per_sm[2] = {0, 0};
+    const int key = smem > 48 * 1024 ? 1 : 0;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_stream_large<ONE, ADV, HOT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (per_sm[key] == 0) {
+      int b = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stream_large<ONE, ADV, HOT>, kBlock, smem);
+      if (e != cudaSuccess) return e;
+      per_sm[key] = b > 0 ? b : 1;
+    }
+    const uint64_t n_se = (uint64_t)d.r << d.q;
+    uint64_t need = (n_se + (kBlock / 32) - 1) / (kBlock / 32);
+    uint64_t grid = (uint64_t)sms * per_sm[key];
+    if (grid > need) grid = need;
+    k_stream_large<ONE, ADV, HOT><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+  } else {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int b = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stream_small<ONE, ADV, HOT>, kBlock, 0);
+      if (e != cudaSuccess) return e;
+      per_sm = b > 0 ? b : 1;
+    }
+    const uint64_t n_units = (((uint64_t)d.r << d.q) * d.eta) / 256;
+    uint64_t need = (n_units + (kBlock / 32) - 1) / (kBlock / 32);
+    uint64_t grid = (uint64_t)sms * per_sm;
+    if (grid > need) grid = need;
+    k_stream_small<ONE, ADV, HOT><<<(unsigned)grid, kBlock, 0, st>>>(d, s, a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
+                          cudaStream_t st) {
+  const bool one = a.n == 1, adv = (mode & kAdvance) != 0, hot = (mode & kHot) != 0;
+#define SSD_STREAM_CASE(O, A, H) \
+  if (one == O && adv == A && hot == H) return launch_variant<O, A, H>(d, s, a, sms, st);
+  SSD_STREAM_CASE(true, true, true)
+  SSD_STREAM_CASE(true, true, false)
+  SSD_STREAM_CASE(true, false, true)
+  SSD_STREAM_CASE(true, false, false)
+  SSD_STREAM_CASE(false, true, true)
+  SSD_STREAM_CASE(false, true, false)
+  SSD_STREAM_CASE(false, false, true)
+  SSD_STREAM_CASE(false, false, false)
+#undef SSD_STREAM_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ssd
