@@ -332,6 +332,8 @@ def run_ours(args, world, rank, local):
         t_start.record(stream)
         for i in range(args.steps):
             e = E[i]
+            for ev in e[2:]:
+                ev.record(stream)   # torch marks them recorded; the library re-records them in place
             ctx.set_trace(e[2], e[3], e[4])
             step(fill + args.warmup + i, ev=e)
         t_end.record(stream)
