@@ -56,6 +56,12 @@ WORKLOADS = {
         traffic=dict(seed=1005, n_src=1_000_000, zipf_s=1.1, deg_cap=512, rho=0.3, n_planted=20,
                      planted_lo=1500, planted_hi=50_000, k=60, planted_mode=1, count="uniform",
                      count_a=10_000, count_b=2_000_000)),
+    # The core-link recipe at q=16 (a 1.25 GiB RSEA, still ten times L2) for profiler captures.
+    "corelink_prof": dict(
+        params=_p(11, 16, 5, 6, 60, 1024), hash_seed=12, slots=12,
+        traffic=dict(seed=1012, n_src=250_000, zipf_s=1.1, deg_cap=512, rho=0.3, n_planted=50,
+                     planted_lo=1500, planted_hi=50_000, k=60, planted_mode=1, count="fixed",
+                     count_a=1_562_500)),
     # ---- reduced sizes of the same recipes (element-by-element parity) ----
     "corelink_small": dict(
         params=_p(11, 14, 5, 6, 8, 1024), hash_seed=22, slots=14,
