@@ -188,6 +188,29 @@ SSD_API int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, voi
 SSD_API int ssd_regain(ssd_ctx* ctx, const ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap,
                uint64_t* n_out, void* stream);
 
+/* The regain of ssd_regain for callers that cannot allocate device memory: a
+ * process whose device memory is already claimed by another framework's
+ * caching allocator, or a datapath that must not pay cudaMalloc's implicit
+ * device synchronisation. It needs no context and allocates nothing: its
+ * scratch is one fixed 32 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits. (The paper has no
+ * counterpart; this is a deployment variant of the same computation.)
+ *   p: the parameter set (its capacity fields are ignored: the array decides
+ *      them, at most 4096 hot estimators per row);
+ *   d_tables: the 2048 hash-table words of ssd_create, in device memory;
+ *   d_recorders: a whole RSEA (ssd_sketch_bytes bytes, 16-byte aligned) in
+ *      device memory on the current device;
+ *   d_ips, d_rk, cap, *n_out: as in ssd_regain.
+ * Runs on the caller's current device and waits for `stream`. The first call
+ * on a device looks up the array's device address (once per device); make that
+ * first call before any stream capture. Returns SSD_ECAPACITY when the
+ * parameter set needs more scratch than the array holds (r * 2^q four-byte
+ * entries must stay under 16 MiB: q <= 19 at r = 5) or when a capacity overflowed. Every
+ * call shares the one array and leaves its contents behind; calls that overlap
+ * on the GPU race and must be serialised by the caller. */
+SSD_API int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, const uint16_t* d_recorders,
+                              uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* n_out, void* stream);
+
 /* End of slot for n routers, fully asynchronous and free of host
  * synchronisation (it can be captured in a CUDA graph): one streaming pass
  * merges the routers (Algorithm 5, min reading), writes the merged RSEA to

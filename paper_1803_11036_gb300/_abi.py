@@ -52,6 +52,7 @@ SIGNATURES = {
     "ssd_advance": ([_vp, _int, _vp], _int),
     "ssd_merge": ([_vp, _int, _vp, _vp], _int),
     "ssd_regain": ([_vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
+    "ssd_regain_static": ([_PP, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_close_slot": ([_vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_set_trace": ([_vp, _vp, _vp, _vp], _int),
     "ssd_stats_get": ([_vp, ctypes.POINTER(Stats), _vp], _int),
