@@ -41,13 +41,14 @@ PAPER_PACKET_BYTES = 800
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--fill", type=int, default=-1, help="untimed slots before warm-up (default: k)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -74,30 +75,40 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def _reduce(x: float, world: int, op: str) -> float:
+    """Max or sum of a float over the ranks (CUDA tensors under NCCL, CPU tensors under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return _reduce(x, world, "max")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, "sum")
+
+
+def replica_workload(name: str, rank: int) -> dict:
+    """The workload a rank runs: the same parameters, an independent traffic seed per rank."""
+    import trafficgen as tg
+    W = tg.workload(name)
+    W["_name"] = name
+    if rank:
+        W["traffic"]["seed"] += 7919 * rank
+    return W
 
 
 # ------------------------------------------------------------------ clocks
 
 class Clocks:
-    """nvidia-smi samples during the timed region (every 200 ms)."""
+    """nvidia-smi samples during the timed region (every 50 ms)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -113,7 +124,7 @@ class Clocks:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -264,6 +275,71 @@ def run_reference(args, world, rank):
 
 # -------------------------------------------------------------- our arm
 
+def batched_vs_plain(rank: int, local: int, name: str = "edge16_c3", fill: int = 4, warmup: int = 2,
+                     steps: int = 5) -> dict:
+    """The same slots of a many-router workload two ways, with identical lists required.
+    plain: one ssd_scan per router, then ssd_merge, ssd_regain and ssd_advance;
+    batched: one ssd_scan_batch over all routers, then one ssd_close_slot."""
+    import torch
+
+    import paper_1803_11036_gb300 as ssd
+    import trafficgen as tg
+
+    dev = torch.device("cuda", local)
+    W = replica_workload(name, rank)
+    T = tg.Traffic(**W["traffic"])
+    R = T.routers
+    n = fill + warmup + steps
+    slots = []
+    for t in range(n):
+        slots.append([torch.from_numpy(v.reshape(-1).view(np.int32)).to(dev) for v in T.slot(t)])
+    pk = [sum(x.numel() // 2 for x in s) for s in slots]
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    lists = {}
+    for mode in ("plain", "batched"):
+        ctx = ssd.Context(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]), device=local)
+        routers = [ctx.sketch() for _ in range(R)]
+        glob = ctx.sketch() if mode == "plain" else None
+        got = []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = 0
+        with torch.cuda.stream(stream):
+            for t in range(n):
+                if t == fill + warmup:
+                    stream.synchronize()
+                    l0 = ctx.launch_count
+                    a.record(stream)
+                if mode == "plain":
+                    for sk, x in zip(routers, slots[t]):
+                        ctx.scan(sk, x, stream=stream)
+                    ctx.merge(routers, glob, stream=stream)
+                    lst = ctx.regain(glob, stream=stream)
+                    ctx.advance(routers, stream=stream)
+                else:
+                    ctx.scan_batch(routers, slots[t], stream=stream)
+                    lst = ctx.close_slot(routers, None, stream=stream)
+                if t >= fill + warmup:
+                    got.append(lst)
+            b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[mode] = {"ms_per_slot": round(ms, 3), "launches_per_slot": (ctx.launch_count - l0) / steps}
+        lists[mode] = got
+        del routers, glob
+        ctx.close()
+        torch.cuda.empty_cache()
+    same = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+               for x, y in zip(lists["plain"], lists["batched"]))
+    timed = sum(pk[fill + warmup:])
+    return {"workload": name, "routers": R, "packets_per_slot_mean": int(timed / steps),
+            "plain": {**out["plain"], "mpps": round(timed / (out["plain"]["ms_per_slot"] * steps) / 1e3, 1)},
+            "batched": {**out["batched"], "mpps": round(timed / (out["batched"]["ms_per_slot"] * steps) / 1e3, 1)},
+            "speedup": round(out["plain"]["ms_per_slot"] / out["batched"]["ms_per_slot"], 3),
+            "identical_lists": bool(same), "window_filled_slots": fill,
+            "note": "plain = per-router scans + merge + regain + advance; batched = one scan launch + fused close"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -272,10 +348,7 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    W = tg.workload(args.workload)
-    W["_name"] = args.workload
-    if rank:
-        W["traffic"]["seed"] += 7919 * rank   # an independent replica per rank
+    W = replica_workload(args.workload, rank)
     prm = W["params"]
     k = prm["k"]
     fill = k if args.fill < 0 else args.fill
@@ -393,6 +466,11 @@ def run_ours(args, world, rank, local):
                "d2h_bytes_per_step": int(d2h / args.steps)}
         del host
 
+    del slot_dev, routers
+    ctx.close()
+    torch.cuda.empty_cache()
+    bvp = None if args.no_batched else batched_vs_plain(rank, local)
+
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(W)
@@ -411,7 +489,7 @@ def run_ours(args, world, rank, local):
         "reconstruct_ms_per_slice": {"close_pass": round(statistics.mean(pass_ms), 4),
                                      "candidates_and_list": round(statistics.mean(tail_ms), 4),
                                      "total": round(statistics.mean(pass_ms) + statistics.mean(tail_ms), 4)},
-        "batched_vs_plain": None,
+        "batched_vs_plain": bvp,
         "roofline": {"kernel": "k_stream_large<one router, advance, hot> (merge + hot extraction + advance)",
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
