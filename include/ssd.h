@@ -73,6 +73,7 @@ extern "C" {
  *   hse_capacity: hot estimators kept per row (0 = min(2^q, 65536))
  *   ctb_capacity: tuples per candidate tuple buffer (0 = 2^22)
  *   out_capacity: accepted tuples staged before the list is sorted (0 = 2^20)
+ *   touch_chunk_bytes: touch bits per chunk of ssd_slot, kept in L2 (0 = 32 MiB)
  */
 typedef struct ssd_params {
   uint32_t log2_eta;
@@ -85,6 +86,7 @@ typedef struct ssd_params {
   uint32_t hse_capacity;
   uint64_t ctb_capacity;
   uint64_t out_capacity;
+  uint64_t touch_chunk_bytes;
 } ssd_params;
 
 typedef struct ssd_ctx ssd_ctx;
@@ -229,6 +231,34 @@ SSD_API int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_
  * are cudaEvent_t passed as void*, created by the caller; NULLs switch tracing
  * off. */
 SSD_API int ssd_set_trace(ssd_ctx* ctx, void* ev_start, void* ev_pass, void* ev_end);
+
+/* A whole slot for n routers in one call: Algorithm 2 for every router's pairs
+ * followed by the end of slot of ssd_close_slot - the same result as
+ * ssd_scan_batch(routers, d_pairs, n_pairs, n) then ssd_close_slot(...), with
+ * the same arguments and the same asynchrony (no host synchronisation).
+ * The recorders are not written by the scan: the estimators are taken in
+ * chunks whose touch bits (one bit per recorder and router, touch_chunk_bytes
+ * per chunk, double-buffered) stay in L2; a side stream collects the touches of
+ * chunk c+1 while the streaming pass applies those of chunk c (recorder := 0,
+ * Sec. 4.1), merges, extracts the hot estimators and advances. Every recorder
+ * is read and written once per slot and no random DRAM write remains. When the
+ * routers' touch bits would need more than 16 chunks the call runs
+ * ssd_scan_batch and ssd_close_slot instead (same result). */
+SSD_API int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs,
+                     const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
+                     uint64_t cap, uint64_t* d_n_out, void* stream);
+
+/* ssd_slot on pairs held in HOST memory (pinned for overlap): each router's
+ * pairs are copied on an internal copy stream into one of two context-owned
+ * device staging areas (the alpha-pair buffer of Sec. 4.1, sized to the slot),
+ * then ssd_slot runs on `stream`. The copy of one call overlaps the slots still
+ * running from earlier calls. With pinned memory the call returns before the
+ * copies finish: keep h_pairs unchanged until `stream` has passed this call. A
+ * slot larger than any earlier one (re)allocates the staging areas, waiting for
+ * the context's work first; make the first call before any stream capture. */
+SSD_API int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* h_pairs,
+                          const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
+                          uint64_t cap, uint64_t* d_n_out, void* stream);
 
 /* Counters of the context's last regain or close (waits for `stream`). */
 SSD_API int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream);

@@ -36,10 +36,10 @@ def library_path() -> str:
 
 
 def make_params(d: dict, flags: int = 0, hse_capacity: int = 0, ctb_capacity: int = 0,
-                out_capacity: int = 0) -> Params:
+                out_capacity: int = 0, touch_chunk_bytes: int = 0) -> Params:
     """Params from a dict with log2_eta, q, r, delta, k, theta (and optional flags)."""
     return Params(d["log2_eta"], d["q"], d["r"], d["delta"], d["k"], d["theta"], d.get("flags", 0) | flags,
-                  hse_capacity, ctb_capacity, out_capacity)
+                  hse_capacity, ctb_capacity, out_capacity, touch_chunk_bytes)
 
 
 def params_ok(p: Params) -> bool:
@@ -243,6 +243,79 @@ class Context:
         s = self.stats(stream)
         if s["status"]:
             raise SSDError(SSD_ECAPACITY, f"ssd_close_slot (status {s['status']})")
+        m = int(n_out.item())
+        return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
+
+    def slot(self, routers, pairs_list, global_sketch: Sketch | None = None, cap: int = 1 << 16, out=None,
+             stream=None, sync: bool = True):
+        """A whole slot: scan every router's pairs, then merge, regain and advance (one call,
+        touches kept in L2). Same result and return convention as scan_batch + close_slot."""
+        if len(routers) != len(pairs_list):
+            raise ValueError("one pair tensor per router")
+        ptrs, counts = [], []
+        for t in pairs_list:
+            p, n = _pairs_ptr(t, self.device)
+            ptrs.append(p.value or 0)
+            counts.append(n)
+        P = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        N = (ctypes.c_uint64 * len(counts))(*counts)
+        if out is None:
+            ips, rk = self._outputs(cap)
+            n_out = self._n_out
+        else:
+            ips, rk, n_out = out
+            cap = min(ips.numel(), rk.numel())
+        st = _stream_handle(stream, self.device)
+        check(self.L.ssd_slot(self._h, _handles(routers), P, N, len(routers),
+                              global_sketch._h if global_sketch is not None else None,
+                              ctypes.c_void_p(ips.data_ptr()), ctypes.c_void_p(rk.data_ptr()), cap,
+                              ctypes.c_void_p(n_out.data_ptr()), st), "ssd_slot")
+        if not sync:
+            return ips, rk, n_out
+        s = self.stats(stream)
+        if s["status"]:
+            raise SSDError(SSD_ECAPACITY, f"ssd_slot (status {s['status']})")
+        m = int(n_out.item())
+        return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
+
+    def slot_host(self, routers, host_pairs, global_sketch: Sketch | None = None, cap: int = 1 << 16, out=None,
+                  stream=None, sync: bool = True):
+        """slot() on pairs in host memory: (n, 2) uint32 numpy arrays or CPU tensors (pinned for
+        overlap; keep them unchanged until the stream has passed this call)."""
+        torch = _torch()
+        if len(routers) != len(host_pairs):
+            raise ValueError("one pair buffer per router")
+        ptrs, counts, keep = [], [], []
+        for h in host_pairs:
+            if isinstance(h, torch.Tensor):
+                if h.is_cuda or h.element_size() != 4 or not h.is_contiguous():
+                    raise ValueError("host pairs: contiguous CPU tensor of 4-byte integers")
+                ptrs.append(h.data_ptr() if h.numel() else 0)
+                counts.append(h.numel() // 2)
+            else:
+                a = np.ascontiguousarray(h, dtype=np.uint32)
+                keep.append(a)
+                ptrs.append(a.ctypes.data if a.size else 0)
+                counts.append(a.size // 2)
+        self._host_keep = keep
+        P = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        N = (ctypes.c_uint64 * len(counts))(*counts)
+        if out is None:
+            ips, rk = self._outputs(cap)
+            n_out = self._n_out
+        else:
+            ips, rk, n_out = out
+            cap = min(ips.numel(), rk.numel())
+        st = _stream_handle(stream, self.device)
+        check(self.L.ssd_slot_host(self._h, _handles(routers), P, N, len(routers),
+                                   global_sketch._h if global_sketch is not None else None,
+                                   ctypes.c_void_p(ips.data_ptr()), ctypes.c_void_p(rk.data_ptr()), cap,
+                                   ctypes.c_void_p(n_out.data_ptr()), st), "ssd_slot_host")
+        if not sync:
+            return ips, rk, n_out
+        s = self.stats(stream)
+        if s["status"]:
+            raise SSDError(SSD_ECAPACITY, f"ssd_slot_host (status {s['status']})")
         m = int(n_out.item())
         return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
 

@@ -23,7 +23,8 @@ class Params(ctypes.Structure):
     _fields_ = [("log2_eta", ctypes.c_uint32), ("q", ctypes.c_uint32), ("r", ctypes.c_uint32),
                 ("delta", ctypes.c_uint32), ("k", ctypes.c_uint32), ("theta", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("hse_capacity", ctypes.c_uint32),
-                ("ctb_capacity", ctypes.c_uint64), ("out_capacity", ctypes.c_uint64)]
+                ("ctb_capacity", ctypes.c_uint64), ("out_capacity", ctypes.c_uint64),
+                ("touch_chunk_bytes", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -54,6 +55,8 @@ SIGNATURES = {
     "ssd_regain": ([_vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_regain_static": ([_PP, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_close_slot": ([_vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
+    "ssd_slot": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
+    "ssd_slot_host": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_set_trace": ([_vp, _vp, _vp, _vp], _int),
     "ssd_stats_get": ([_vp, ctypes.POINTER(Stats), _vp], _int),
     "ssd_launch_count": ([_vp], _u64),

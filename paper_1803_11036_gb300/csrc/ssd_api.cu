@@ -30,6 +30,16 @@ struct ssd_ctx {
   uint64_t stage_alpha;
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_scanned[2];
+  // fused slot: double-buffered touch bits and the side stream that fills them
+  uint32_t* touch[2];
+  uint64_t touch_bytes;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_touched[2], ev_closed[2];
+  // host-pair staging of ssd_slot_host (double-buffered, sized to the largest slot)
+  uint32_t* hs_buf[2];
+  uint64_t hs_bytes;
+  uint64_t hs_calls;
+  cudaEvent_t ev_hs_free[2], ev_hs_copied;
 };
 
 struct ssd_sketch {
@@ -160,10 +170,21 @@ void free_ctx(ssd_ctx* c) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
   }
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_hs_copied) cudaEventDestroy(c->ev_hs_copied);
   for (int i = 0; i < 2; ++i) {
     if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     if (c->ev_scanned[i]) cudaEventDestroy(c->ev_scanned[i]);
+    if (c->ev_touched[i]) cudaEventDestroy(c->ev_touched[i]);
+    if (c->ev_closed[i]) cudaEventDestroy(c->ev_closed[i]);
     cudaFree(c->stage_pairs[i]);
+    cudaFree(c->touch[i]);
+    if (c->ev_hs_free[i]) cudaEventDestroy(c->ev_hs_free[i]);
+    cudaFree(c->hs_buf[i]);
   }
   cudaFree(c->tables);
   cudaFree(c->hot_idx);
@@ -249,7 +270,11 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   d.out_cap = pow2_at_least(p->out_capacity ? p->out_capacity : (1ull << 20));
 
   const uint64_t R = p->r;
+  c->touch_bytes = p->touch_chunk_bytes ? p->touch_chunk_bytes : (32ull << 20);
+  c->touch_bytes = (c->touch_bytes + 255) & ~255ull;
   struct Alloc { void** ptr; uint64_t bytes; } allocs[] = {
+      {(void**)&c->touch[0], c->touch_bytes},
+      {(void**)&c->touch[1], c->touch_bytes},
       {(void**)&c->tables, 2048 * 4},
       {(void**)&c->hot_idx, R * C * 4},
       {(void**)&c->pool_col, R * d.hse_cap * 4},
@@ -270,6 +295,15 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   }
   e = cudaMemcpy(c->tables, tables, 2048 * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(ssd::DevCounters));
+  // touch bits start (and are left by every fused slot) all zero
+  if (e == cudaSuccess) e = cudaMemset(c->touch[0], 0, c->touch_bytes);
+  if (e == cudaSuccess) e = cudaMemset(c->touch[1], 0, c->touch_bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&c->ev_touched[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_closed[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "ssd_create"); }
   c->s.tables = c->tables;
@@ -497,6 +531,138 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   const uint64_t merged = routers[0]->slot;
   for (int i = 0; i < n; ++i) routers[i]->slot += 1;
   if (global) global->slot = merged;
+  return SSD_OK;
+}
+
+int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs, const uint64_t* n_pairs,
+             int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out,
+             void* stream) {
+  ssd_ctx* c2 = nullptr;
+  if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx || !d_pairs || !n_pairs) return SSD_EINVAL;
+  if (global && global->ctx != ctx) return SSD_EINVAL;
+  if (cap && (!d_ips || !d_rk)) return SSD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (routers[i] == global) return SSD_EINVAL;
+    if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
+    for (int j = 0; j < i; ++j)
+      if (routers[j] == routers[i]) return SSD_EINVAL;
+  }
+  const ssd::Dims& d = ctx->d;
+  const uint64_t n_se = (uint64_t)d.r << d.q;
+  const uint64_t se_bytes = (uint64_t)n * (d.eta >> 3);  // touch bytes of one estimator, all routers
+  uint64_t count = 1;
+  while (count * 2 * se_bytes <= ctx->touch_bytes && count * 2 <= pow2_at_least(n_se)) count *= 2;
+  const uint64_t n_chunks = (n_se + count - 1) / count;
+  if (count * se_bytes > ctx->touch_bytes || count < 8 || n_chunks > 16) {
+    int rc = ssd_scan_batch(routers, d_pairs, n_pairs, n, stream);
+    if (rc != SSD_OK) return rc;
+    return ssd_close_slot(ctx, routers, n, global, d_ips, d_rk, cap, d_n_out, stream);
+  }
+  ssd::ScanBatch b;
+  std::memset(&b, 0, sizeof(b));
+  b.n = n;
+  uint64_t prefix = 0;
+  for (int j = 0; j < n; ++j) {
+    int rc = add_job(b, j, routers[j]->dr, d_pairs[j], n_pairs[j], &prefix);
+    if (rc != SSD_OK) return rc;
+  }
+  b.prefix[n] = prefix;
+  uint64_t tgrid = (prefix + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
+  if (tgrid > (uint64_t)ctx->sms * 8) tgrid = (uint64_t)ctx->sms * 8;
+  if (tgrid < 1) tgrid = 1;
+
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
+  int rc = trace(ctx, ctx->tr_start, st);
+  if (rc != SSD_OK) return rc;
+  SSD_CUDA(cudaEventRecord(ctx->ev_fork, st));
+  SSD_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  ssd::StreamArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  for (int i = 0; i < n; ++i) a.routers[i] = routers[i]->dr;
+  a.global = global ? global->dr : nullptr;
+  for (uint64_t c = 0; c < n_chunks; ++c) {
+    const int bsel = (int)(c & 1);
+    const uint64_t se0 = c * count;
+    const uint64_t cnt = n_se - se0 < count ? n_se - se0 : count;
+    if (c >= 2) SSD_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_closed[bsel], 0));  // buffer cleared
+    cudaError_t e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[bsel], se0, cnt, (int)tgrid, ctx->side);
+    if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
+    ctx->launches += 1;
+    SSD_CUDA(cudaEventRecord(ctx->ev_touched[bsel], ctx->side));
+    SSD_CUDA(cudaStreamWaitEvent(st, ctx->ev_touched[bsel], 0));
+    a.se0 = se0;
+    a.se_count = cnt;
+    a.touch = reinterpret_cast<uint8_t*>(ctx->touch[bsel]);
+    e = ssd::launch_stream(d, ctx->s, a, ssd::kAdvance | ssd::kHot, ctx->sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream kernel");
+    ctx->launches += 1;
+    SSD_CUDA(cudaEventRecord(ctx->ev_closed[bsel], st));
+  }
+  rc = trace(ctx, ctx->tr_pass, st);
+  unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
+  if (rc != SSD_OK) return rc;
+  const uint64_t merged = routers[0]->slot;
+  for (int i = 0; i < n; ++i) routers[i]->slot += 1;
+  if (global) global->slot = merged;
+  return SSD_OK;
+}
+
+int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* h_pairs,
+                  const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
+                  uint64_t cap, uint64_t* d_n_out, void* stream) {
+  ssd_ctx* c2 = nullptr;
+  if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx || !h_pairs || !n_pairs) return SSD_EINVAL;
+  uint64_t off[SSD_MAX_ROUTERS + 1];
+  off[0] = 0;
+  for (int j = 0; j < n; ++j) {
+    if (n_pairs[j] && !h_pairs[j]) return SSD_EINVAL;
+    off[j + 1] = off[j] + ((n_pairs[j] * 8 + 15) & ~15ull);  // 16-byte aligned start per router
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  if (!ctx->copy_stream) SSD_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->ev_hs_copied) {
+    SSD_CUDA(cudaEventCreateWithFlags(&ctx->ev_hs_copied, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) SSD_CUDA(cudaEventCreateWithFlags(&ctx->ev_hs_free[i], cudaEventDisableTiming));
+  }
+  if (off[n] > ctx->hs_bytes) {  // grow the staging areas (waits for the work using them)
+    SSD_CUDA(cudaStreamSynchronize(ctx->copy_stream));
+    SSD_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < 2; ++i) {
+      SSD_CUDA(cudaEventSynchronize(ctx->ev_hs_free[i]));
+      cudaFree(ctx->hs_buf[i]);
+      ctx->hs_buf[i] = nullptr;
+    }
+    const uint64_t want = off[n] + off[n] / 4 + 256;
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&ctx->hs_buf[i], want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hs_bytes = 0;
+        return SSD_ENOMEM;
+      }
+    }
+    ctx->hs_bytes = want;
+  }
+  const int b = (int)(ctx->hs_calls & 1);
+  SSD_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_hs_free[b], 0));  // the slot two calls back is done
+  const uint32_t* dp[SSD_MAX_ROUTERS];
+  unsigned char* base = reinterpret_cast<unsigned char*>(ctx->hs_buf[b]);
+  for (int j = 0; j < n; ++j) {
+    dp[j] = reinterpret_cast<const uint32_t*>(base + off[j]);
+    if (n_pairs[j])
+      SSD_CUDA(cudaMemcpyAsync(base + off[j], h_pairs[j], n_pairs[j] * 8, cudaMemcpyHostToDevice, ctx->copy_stream));
+  }
+  SSD_CUDA(cudaEventRecord(ctx->ev_hs_copied, ctx->copy_stream));
+  SSD_CUDA(cudaStreamWaitEvent(st, ctx->ev_hs_copied, 0));
+  int rc = ssd_slot(ctx, routers, dp, n_pairs, n, global, d_ips, d_rk, cap, d_n_out, stream);
+  if (rc != SSD_OK) return rc;
+  SSD_CUDA(cudaEventRecord(ctx->ev_hs_free[b], st));
+  ctx->hs_calls += 1;
   return SSD_OK;
 }
 

@@ -69,12 +69,24 @@ struct StreamArgs {
   int n;                               // routers
   uint16_t* routers[kMaxBatch];
   uint16_t* global;                    // merged output, or nullptr
+  uint64_t se0;                        // first estimator of the pass
+  uint64_t se_count;                   // estimators in the pass; 0 = all r * 2^q from se0 = 0
+  uint8_t* touch;                      // touch bits of the pass's estimators per router, or nullptr:
+                                       // router j, estimator se0 + e, recorder x at bit
+                                       // (j * se_count + e) * eta + x; applied (recorder := 0) and cleared
 };
 // mode bits
 constexpr int kAdvance = 1;   // routers += 1 (saturating) after reading
 constexpr int kHot = 2;       // count R_k of the merged value and pool the hot estimators
+// spare_blocks: resident blocks per SM left free for a concurrent kernel (0 = none)
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
-                          cudaStream_t st);
+                          cudaStream_t st, int spare_blocks = 0);
+
+// ---- touch collection for the fused slot (ssd_scan.cu) ----
+// Algorithm 2 for the estimators [se0, se0 + se_count) only: instead of storing
+// 0 into the recorder, set its bit in `bits` (layout of StreamArgs::touch).
+cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
+                         uint64_t se_count, int grid, cudaStream_t st);
 
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.

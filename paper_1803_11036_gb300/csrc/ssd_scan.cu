@@ -103,7 +103,75 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
   }
 }
 
+// Algorithm 2 for the estimators [se0, se0 + count) of one chunk: the recorder a
+// pair sets to 0 is marked in `bits` instead (router j, estimator se0 + e,
+// recorder x -> bit (j * count + e) * eta + x). The chunk lies in one row or
+// covers whole rows, so a pair has at most one touch per row of the chunk.
+__device__ __forceinline__ void touch_pair(uint32_t* __restrict__ bits, uint64_t jbase, uint32_t cip, uint32_t oip,
+                                           const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
+                                           uint64_t se0, uint64_t count) {
+  const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
+  uint32_t x = 0xFFFFFFFFu;
+  for (uint32_t i = r0; i <= r1; ++i) {
+    uint32_t col = c0;
+    if (i) {
+      const uint32_t sh = (i - 1u) * d.delta;
+      col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
+    }
+    const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
+    if (e < count) {
+      if (x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
+      const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
+      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* __restrict__ tables,
+                                                  const __grid_constant__ ScanBatch b, uint32_t* __restrict__ bits,
+                                                  uint64_t se0, uint64_t count) {
+  __shared__ uint32_t sT[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
+  __syncthreads();
+  const uint32_t r0 = (uint32_t)(se0 >> d.q), r1 = (uint32_t)((se0 + count - 1) >> d.q);
+  if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
+    const uint32_t* e = b.edge[threadIdx.x];
+    if (e) touch_pair(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], sT, d, r0, r1, se0, count);
+  }
+  const uint64_t total = b.prefix[b.n];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
+    uint4 w[kUnroll];
+    uint64_t jb[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t vv = v + u * stride;
+      const int j = b.n == 1 ? 0 : find_router(b, vv);
+      w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
+      jb[u] = (uint64_t)j * count;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      touch_pair(bits, jb[u], w[u].x, w[u].y, sT, d, r0, r1, se0, count);
+      touch_pair(bits, jb[u], w[u].z, w[u].w, sT, d, r0, r1, se0, count);
+    }
+  }
+  for (; v < total; v += stride) {
+    const int j = b.n == 1 ? 0 : find_router(b, v);
+    const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
+    touch_pair(bits, (uint64_t)j * count, w.x, w.y, sT, d, r0, r1, se0, count);
+    touch_pair(bits, (uint64_t)j * count, w.z, w.w, sT, d, r0, r1, se0, count);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
+                         uint64_t se_count, int grid, cudaStream_t st) {
+  k_touch<<<grid, kBlock, 0, st>>>(d, tables, b, bits, se0, se_count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, cudaStream_t st) {
   static_assert(sizeof(ScanBatch) < 32000, "kernel parameter block too large");

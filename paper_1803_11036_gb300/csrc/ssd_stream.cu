@@ -2,12 +2,15 @@
 // extraction (Sec. 3.3) and the distance recorder update (Sec. 4.3).
 //
 // One kernel serves every combination: for each recorder position it reads the
-// n routers' values (16 bytes = 8 recorders per lane), takes their elementwise
-// minimum (the merge), optionally writes that to the global RSEA, optionally
-// counts the merged recorders below k per estimator and pools the hot ones with
-// their "recorder < k" bitmap, and optionally writes every router's value back
-// advanced by one with saturation at 65535. Recorders are read and written once
-// per pass, in 512-byte coalesced warp accesses with streaming cache hints.
+// n routers' values (16 bytes = 8 recorders per lane), optionally sets the
+// recorders whose touch bit is set to 0 first (Algorithm 2 deferred from the
+// scan of the fused slot; the bit is cleared), takes the elementwise minimum
+// over routers (the merge), optionally writes that to the global RSEA,
+// optionally counts the merged recorders below k per estimator and pools the hot
+// ones with their "recorder < k" bitmap, and optionally writes every router's
+// value back advanced by one with saturation at 65535. Recorders are read and
+// written once per pass, in 512-byte coalesced warp accesses with streaming
+// cache hints; the touch bits stay in L2.
 #include "ssd_internal.cuh"
 
 namespace ssd {
@@ -30,6 +33,13 @@ __device__ __forceinline__ uint32_t lt2(uint32_t w, uint32_t kk) {
 __device__ __forceinline__ uint32_t lt8(uint4 v, uint32_t kk) {
   return lt2(v.x, kk) | (lt2(v.y, kk) << 2) | (lt2(v.z, kk) << 4) | (lt2(v.w, kk) << 6);
 }
+// recorders whose bit is set in t (bit i = recorder i of the 8) become 0
+__device__ __forceinline__ uint32_t zero2(uint32_t w, uint32_t t2) {
+  return w & ~(((t2 & 1u) * 0xFFFFu) | ((t2 >> 1) * 0xFFFF0000u));
+}
+__device__ __forceinline__ uint4 apply8(uint4 v, uint32_t t) {
+  return make_uint4(zero2(v.x, t & 3u), zero2(v.y, (t >> 2) & 3u), zero2(v.z, (t >> 4) & 3u), zero2(v.w, t >> 6));
+}
 
 // Pool a hot estimator: reserve a slot in its row's pool and return it
 // (kNone when the pool is full).
@@ -42,34 +52,54 @@ __device__ __forceinline__ uint32_t pool_slot(const Dims& d, const Scratch& s, u
   return idx;
 }
 
+// Touch bits of router j for 8 recorders (one byte), cleared after reading.
+__device__ __forceinline__ uint32_t take_touch(uint8_t* p) {
+  const uint32_t t = *p;
+  if (t) *p = 0;
+  return t;
+}
+
 // eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
-template <bool ONE, bool ADV, bool HOT>
-__global__ void __launch_bounds__(kBlock) k_stream_large(const Dims d, const Scratch s,
+template <bool ONE, bool ADV, bool HOT, bool TOUCH>
+__global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) uint8_t smask[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* my = smask + (size_t)wid * (d.eta >> 3);
-  const uint64_t n_se = (uint64_t)d.r << d.q;
+  const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
+  const uint64_t se_end = a.se0 + count;
   const uint32_t iters = d.eta >> 8;
   const uint32_t kk = d.k | (d.k << 16);
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  const uint64_t tstride = count * (d.eta >> 3);  // touch bytes per router
   uint4* const g = reinterpret_cast<uint4*>(a.global);
 
-  for (uint64_t se = (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < n_se; se += wstride) {
+  for (uint64_t se = a.se0 + (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < se_end; se += wstride) {
     const uint64_t base = (se << d.log2_eta) >> 3;  // in 8-recorder units
+    uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane : nullptr;
     uint32_t cnt = 0;
     if (ONE) {
       uint4* const r0 = reinterpret_cast<uint4*>(a.routers[0]);
       for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
         const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
         uint4 v[8];
+        uint32_t t[8];
+        // all loads first (a store in between could alias the next load and serialise them)
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < (int)m) v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
+        for (int u = 0; u < 8; ++u) {
+          if (u < (int)m) {
+            v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
+            if (TOUCH) t[u] = tb[(it0 + u) * 32];
+          }
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           if (u < (int)m) {
             const uint64_t at = base + (it0 + u) * 32 + lane;
+            if (TOUCH) {
+              v[u] = apply8(v[u], t[u]);
+              if (t[u]) tb[(it0 + u) * 32] = 0;
+            }
             if (g) __stcs(g + at, v[u]);
             if (HOT) {
               const uint32_t bits = lt8(v[u], kk);
@@ -85,10 +115,12 @@ __global__ void __launch_bounds__(kBlock) k_stream_large(const Dims d, const Scr
         const uint64_t at = base + it * 32 + lane;
         uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
         uint4 mv = __ldcs(rp + at);
+        if (TOUCH) mv = apply8(mv, take_touch(tb + it * 32));
         if (ADV) __stcs(rp + at, inc8(mv));
         for (int n = 1; n < a.n; ++n) {
           rp = reinterpret_cast<uint4*>(a.routers[n]);
-          const uint4 v = __ldcs(rp + at);
+          uint4 v = __ldcs(rp + at);
+          if (TOUCH) v = apply8(v, take_touch(tb + n * tstride + it * 32));
           mv = min8(mv, v);
           if (ADV) __stcs(rp + at, inc8(v));
         }
@@ -125,28 +157,34 @@ __global__ void __launch_bounds__(kBlock) k_stream_large(const Dims d, const Scr
 }
 
 // 32 <= eta <= 128: L = eta/8 lanes per estimator, 32/L estimators per warp step.
-template <bool ONE, bool ADV, bool HOT>
+template <bool ONE, bool ADV, bool HOT, bool TOUCH>
 __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t L = d.eta >> 3;
   const uint32_t per_warp = 32u / L;
-  const uint64_t n_se = (uint64_t)d.r << d.q;
-  const uint64_t n_units = n_se / per_warp;  // n_se is a multiple of per_warp (2^q >= 2^5)
+  const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
+  const uint64_t u0 = a.se0 / per_warp;         // se0 and count are multiples of per_warp
+  const uint64_t n_units = count / per_warp;
   const uint32_t kk = d.k | (d.k << 16);
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  const uint64_t tstride = count * (d.eta >> 3);
   uint4* const g = reinterpret_cast<uint4*>(a.global);
   uint8_t* const bm_bytes = reinterpret_cast<uint8_t*>(s.pool_bm);
 
-  for (uint64_t u = (uint64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); u < n_units; u += wstride) {
+  for (uint64_t uu = (uint64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); uu < n_units; uu += wstride) {
+    const uint64_t u = u0 + uu;
     const uint64_t at = u * 32 + lane;
+    uint8_t* tb = TOUCH ? a.touch + uu * 32 + lane : nullptr;  // byte of these 8 recorders, router 0
     uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
     uint4 mv = __ldcs(rp + at);
+    if (TOUCH) mv = apply8(mv, take_touch(tb));
     if (ADV) __stcs(rp + at, inc8(mv));
     if (!ONE) {
       for (int n = 1; n < a.n; ++n) {
         rp = reinterpret_cast<uint4*>(a.routers[n]);
-        const uint4 v = __ldcs(rp + at);
+        uint4 v = __ldcs(rp + at);
+        if (TOUCH) v = apply8(v, take_touch(tb + n * tstride));
         mv = min8(mv, v);
         if (ADV) __stcs(rp + at, inc8(v));
       }
@@ -174,41 +212,30 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
   }
 }
 
-template <bool ONE, bool ADV, bool HOT>
-cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a, int sms, cudaStream_t st) {
+template <typename K>
+int blocks_per_sm(K kernel, size_t smem, int spare) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, smem) != cudaSuccess) return 1;
+  b -= spare;
+  return b > 0 ? b : 1;
+}
+
+template <bool ONE, bool ADV, bool HOT, bool TOUCH>
+cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a, int sms, cudaStream_t st,
+                           int spare) {
+  const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
   if (d.eta >= 256) {
     const size_t smem = HOT ? (size_t)(kBlock / 32) * (d.eta >> 3) : 0;
-    static int per_sm[2] = {0, 0};
-    const int key = smem > 48 * 1024 ? 1 : 0;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_stream_large<ONE, ADV, HOT>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    if (per_sm[key] == 0) {
-      int b = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stream_large<ONE, ADV, HOT>, kBlock, smem);
-      if (e != cudaSuccess) return e;
-      per_sm[key] = b > 0 ? b : 1;
-    }
-    const uint64_t n_se = (uint64_t)d.r << d.q;
-    uint64_t need = (n_se + (kBlock / 32) - 1) / (kBlock / 32);
-    uint64_t grid = (uint64_t)sms * per_sm[key];
+    const uint64_t need = (count + (kBlock / 32) - 1) / (kBlock / 32);
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_large<ONE, ADV, HOT, TOUCH>, smem, spare);
     if (grid > need) grid = need;
-    k_stream_large<ONE, ADV, HOT><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+    k_stream_large<ONE, ADV, HOT, TOUCH><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
   } else {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-      int b = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stream_small<ONE, ADV, HOT>, kBlock, 0);
-      if (e != cudaSuccess) return e;
-      per_sm = b > 0 ? b : 1;
-    }
-    const uint64_t n_units = (((uint64_t)d.r << d.q) * d.eta) / 256;
-    uint64_t need = (n_units + (kBlock / 32) - 1) / (kBlock / 32);
-    uint64_t grid = (uint64_t)sms * per_sm;
+    const uint64_t n_units = count * d.eta / 256;
+    const uint64_t need = (n_units + (kBlock / 32) - 1) / (kBlock / 32);
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_small<ONE, ADV, HOT, TOUCH>, 0, spare);
     if (grid > need) grid = need;
-    k_stream_small<ONE, ADV, HOT><<<(unsigned)grid, kBlock, 0, st>>>(d, s, a);
+    k_stream_small<ONE, ADV, HOT, TOUCH><<<(unsigned)grid, kBlock, 0, st>>>(d, s, a);
   }
   return cudaGetLastError();
 }
@@ -216,18 +243,21 @@ cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a,
 }  // namespace
 
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
-                          cudaStream_t st) {
-  const bool one = a.n == 1, adv = (mode & kAdvance) != 0, hot = (mode & kHot) != 0;
-#define SSD_STREAM_CASE(O, A, H) \
-  if (one == O && adv == A && hot == H) return launch_variant<O, A, H>(d, s, a, sms, st);
-  SSD_STREAM_CASE(true, true, true)
-  SSD_STREAM_CASE(true, true, false)
-  SSD_STREAM_CASE(true, false, true)
-  SSD_STREAM_CASE(true, false, false)
-  SSD_STREAM_CASE(false, true, true)
-  SSD_STREAM_CASE(false, true, false)
-  SSD_STREAM_CASE(false, false, true)
-  SSD_STREAM_CASE(false, false, false)
+                          cudaStream_t st, int spare_blocks) {
+  const bool one = a.n == 1, adv = (mode & kAdvance) != 0, hot = (mode & kHot) != 0, touch = a.touch != nullptr;
+#define SSD_STREAM_CASE(O, A, H, T) \
+  if (one == O && adv == A && hot == H && touch == T) \
+    return launch_variant<O, A, H, T>(d, s, a, sms, st, spare_blocks);
+  SSD_STREAM_CASE(true, true, true, false)
+  SSD_STREAM_CASE(true, true, false, false)
+  SSD_STREAM_CASE(true, false, true, false)
+  SSD_STREAM_CASE(true, false, false, false)
+  SSD_STREAM_CASE(false, true, true, false)
+  SSD_STREAM_CASE(false, true, false, false)
+  SSD_STREAM_CASE(false, false, true, false)
+  SSD_STREAM_CASE(false, false, false, false)
+  SSD_STREAM_CASE(true, true, true, true)
+  SSD_STREAM_CASE(false, true, true, true)
 #undef SSD_STREAM_CASE
   return cudaErrorInvalidValue;
 }

@@ -76,5 +76,14 @@ class Run:
         got = self.ctx.close_slot(self.routers, self.glob if with_global else None)
         return got, want
 
+    def step_slot(self, regain_method="levelwise", with_global=True):
+        """Oracle as in step_fused; GPU: one ssd_slot call (scan + close with touches in L2)."""
+        self.t += 1
+        pairs = self.slot_pairs(self.t)
+        want = self.pipe.step(pairs, regain_method)
+        devs = [to_dev(pr) for pr in pairs]
+        got = self.ctx.slot(self.routers, devs, self.glob if with_global else None)
+        return got, want
+
     def close(self):
         self.ctx.close()

@@ -206,6 +206,56 @@ def test_slots_fused_close(wl, with_global):
     run.close()
 
 
+@pytest.mark.parametrize("wl,chunk,with_global", [
+    ("tiny", 0, True),                      # one chunk, eta = 64 (small-estimator kernel)
+    ("tiny", 4096, True),                   # five chunks of one row
+    ("tiny", 1024, False),                  # too many chunks: scan_batch + close_slot
+    ("paper_c1", 0, False),                 # one chunk holding all rows
+    ("paper_c1", 2 << 20, True),            # ten chunks, two per row
+    ("paper_c1", 10 << 20, False),          # three chunks of two rows, the last one partial
+    ("edge_small", 0, True),                # four routers
+    ("stress_small", 16 << 20, False),      # eight routers, hot sources, ten chunks
+    ("stress_small", 64 << 10, False),      # eight routers, fallback
+])
+def test_fused_slot(wl, chunk, with_global):
+    """ssd_slot (touch bits in L2, applied by the streaming pass) gives the oracle's list and
+    merged sketch every slot, and leaves the routers the oracle holds advanced by one."""
+    run = Run(wl, touch_chunk_bytes=chunk)
+    for _ in range(run.W["slots"]):
+        got, want = run.step_slot("pruned", with_global=with_global)
+        assert_list_equal(got, want, f"{wl} slot {run.t}")
+        if with_global:
+            assert np.array_equal(run.glob.export(), run.pipe.global_sk)
+    for r_gpu, r_or in zip(run.routers, run.pipe.routers):
+        nxt = r_or.copy()
+        oracle.advance(run.p, nxt)
+        assert np.array_equal(r_gpu.export(), nxt)
+    run.close()
+
+
+@pytest.mark.parametrize("wl,pinned", [("edge_small", False), ("paper_c1", True)])
+def test_slot_from_host_memory(wl, pinned):
+    """ssd_slot_host (pairs copied from host memory into double-buffered staging that grows with
+    the slot size) gives the oracle's list every slot and leaves the oracle's routers."""
+    import torch
+    run = Run(wl)
+    for _ in range(run.W["slots"]):
+        run.t += 1
+        pairs = run.slot_pairs(run.t)
+        want = run.pipe.step(pairs, "pruned")
+        if pinned:
+            host = [torch.from_numpy(np.ascontiguousarray(x).reshape(-1).view(np.int32)).pin_memory() for x in pairs]
+        else:
+            host = pairs
+        got = run.ctx.slot_host(run.routers, host)
+        assert_list_equal(got, want, f"{wl} slot {run.t}")
+    for r_gpu, r_or in zip(run.routers, run.pipe.routers):
+        nxt = r_or.copy()
+        oracle.advance(run.p, nxt)
+        assert np.array_equal(r_gpu.export(), nxt)
+    run.close()
+
+
 def test_list_capacity_reports_required_size():
     run = Run("paper_c1")
     for _ in range(4):
