@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--touch-chunk-mib", type=int, default=0, help="touch bits per chunk of the fused slot")
     return ap.parse_args()
 
 
@@ -173,9 +174,9 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the streaming pass from the committed ncu summary, if the
-    kernel source has not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"close_pass_{workload}.md")
+    """DRAM bytes per chunk launch of the streaming pass from the committed ncu summary, if
+    the kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"chunk_pass_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -407,7 +408,8 @@ def run_ours(args, world, rank, local):
             slot_dev.append([torch.from_numpy(v.reshape(-1).view(np.int32)).to(dev) for v in views[i:i + R]])
     pk_per_slot = [sum(x.numel() // 2 for x in s) for s in slot_dev]
 
-    ctx = ssd.Context(ssd.make_params(prm), tg.hash_tables(W["hash_seed"]), device=local)
+    ctx = ssd.Context(ssd.make_params(prm, touch_chunk_bytes=args.touch_chunk_mib << 20),
+                      tg.hash_tables(W["hash_seed"]), device=local)
     routers = [ctx.sketch() for _ in range(R)]
     stream = torch.cuda.Stream(dev)
     cap = 1 << 16
@@ -481,6 +483,12 @@ def run_ours(args, world, rank, local):
     pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
     avg_pass_s = statistics.mean(pass_ms) / 1e3
     achieved = pass_bytes / avg_pass_s / 1e9
+    # the pass runs as chunk launches of `chunk` estimators (touch bits of 32 MiB per chunk)
+    n_se = r * C
+    chunk = 1
+    while chunk * 2 * (eta // 8) * R <= (args.touch_chunk_mib << 20 or 32 << 20) and chunk * 2 <= 1 << (n_se - 1).bit_length():
+        chunk *= 2
+    n_chunks = -(-n_se // chunk)
     peak, peak_kind = measured_peak()
     traffic = profiled_traffic(args.workload)
     scan_alg_bytes = 8 + 2 * r                  # pair read + r recorder writes per packet
@@ -523,11 +531,24 @@ def run_ours(args, world, rank, local):
                         d2h += 8 + 2 * 4 * head
             eb.record(stream)
         stream.synchronize()
+        # the host link alone: one slot's pairs, pinned host -> device, 5 times
+        probe = [torch.empty(x.numel(), dtype=x.dtype, device=dev) for x in host[0]]
+        ha, hb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ha.record(stream)
+            for _ in range(5):
+                for dst, src in zip(probe, host[0]):
+                    dst.copy_(src, non_blocking=True)
+            hb_.record(stream)
+        stream.synchronize()
+        h2d_gbs = 5 * sum(x.numel() * 4 for x in host[0]) / (ha.elapsed_time(hb_) / 1e3) / 1e9
+        del probe
         e2e_ms = max_over_ranks(ea.elapsed_time(eb), world)
         e2e = {"value": round(all_pk / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mpps",
                "h2d_bytes_per_step": int(8 * timed_pk / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps),
-               "path": "ssd_slot_host from pinned buffers, list read back every slot"}
+               "path": "ssd_slot_host from pinned buffers, list read back every slot",
+               "host_to_device_gbs": round(h2d_gbs, 1)}
         del host
 
     del slot_dev, routers
@@ -558,11 +579,13 @@ def run_ours(args, world, rank, local):
         "reconstruct_ms_per_slice": round(statistics.mean(tail_ms), 4),
         "batched_vs_plain": bvp,
         "served": served,
-        "roofline": {"kernel": "k_stream_large<one router, advance, hot, touch> chunks (scan touches applied + "
-                               "merge + hot extraction + advance), timed with the touch collection overlapped",
+        "roofline": {"kernel": "k_chunk (one router: the scan's touches applied, hot extraction, advance; the next "
+                               "chunk's touches collected in L2 between estimators), all chunk launches of the pass "
+                               "plus the first chunk's touch launch",
+                     "launches_per_pass": n_chunks, "algorithmic_bytes_per_chunk_launch": chunk * eta * 4 * R,
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch": pass_bytes,
+                     "algorithmic_bytes_per_pass": pass_bytes,
                      "traffic": traffic},
         "hot_per_row": st["hot"], "candidates_per_level": st["level"], "list_size": st["n_out"],
         "gpu_launches": launches,

@@ -59,6 +59,9 @@ extern "C" {
  * levels literally (Algorithms 6-7). The list is identical either way; only the
  * candidate counts (and the work) differ. */
 #define SSD_NO_PRUNE 2u
+/* ssd_slot, one router: collect every chunk's touch bits on the side stream, as
+ * for several routers, instead of inside the streaming kernel. Same result. */
+#define SSD_SLOT_CHUNKED 4u
 
 #define SSD_MAX_R 8
 #define SSD_MAX_ROUTERS 128
@@ -69,7 +72,7 @@ extern "C" {
  *       3 <= r <= SSD_MAX_R, 0 < delta < q <= 24, (r-2)*delta + q >= 32 (Eq. 2-3)
  *   k: window length in slots, 1 <= k <= 65534 (Sec. 3.2)
  *   theta: super point threshold (Def. 2), >= 1
- *   flags: SSD_VERIFY_H0 | SSD_NO_PRUNE
+ *   flags: SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED
  *   hse_capacity: hot estimators kept per row (0 = min(2^q, 65536))
  *   ctb_capacity: tuples per candidate tuple buffer (0 = 2^22)
  *   out_capacity: accepted tuples staged before the list is sorted (0 = 2^20)
@@ -243,7 +246,12 @@ SSD_API int ssd_set_trace(ssd_ctx* ctx, void* ev_start, void* ev_pass, void* ev_
  * Sec. 4.1), merges, extracts the hot estimators and advances. Every recorder
  * is read and written once per slot and no random DRAM write remains. When the
  * routers' touch bits would need more than 16 chunks the call runs
- * ssd_scan_batch and ssd_close_slot instead (same result). */
+ * ssd_scan_batch and ssd_close_slot instead (same result).
+ * One router with eta >= 256 (unless SSD_SLOT_CHUNKED) uses one stream: chunk
+ * 0's bits are collected by one launch, then the streaming kernel of each chunk,
+ * between estimators, also hashes a share of the pairs and collects the next
+ * chunk's bits, so the collection fills the memory stalls of the stream; up to
+ * 32 chunks. */
 SSD_API int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs,
                      const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
                      uint64_t cap, uint64_t* d_n_out, void* stream);

@@ -22,7 +22,8 @@ import weakref
 
 import numpy as np
 
-from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_STATUS_CTB_OVERFLOW,  # noqa: F401
+from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SLOT_CHUNKED,  # noqa: F401
+                   SSD_STATUS_CTB_OVERFLOW,
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
                    Params, SSDError, Stats, check, load)
 

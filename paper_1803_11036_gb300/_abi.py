@@ -14,6 +14,7 @@ from . import _build
 SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECAPACITY, SSD_ECUDA, SSD_ETIMEOUT, SSD_ESTATE = 0, -1, -2, -3, -4, -5, -6
 SSD_VERIFY_H0 = 1
 SSD_NO_PRUNE = 2
+SSD_SLOT_CHUNKED = 4
 SSD_MAX_R = 8
 SSD_MAX_ROUTERS = 128
 SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_CTB_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_STATUS_LIST_OVERFLOW = 1, 2, 4, 8

@@ -186,6 +186,7 @@ void free_ctx(ssd_ctx* c) {
     if (c->ev_hs_free[i]) cudaEventDestroy(c->ev_hs_free[i]);
     cudaFree(c->hs_buf[i]);
   }
+
   cudaFree(c->tables);
   cudaFree(c->hot_idx);
   cudaFree(c->pool_col);
@@ -228,7 +229,7 @@ int ssd_params_check(const ssd_params* p) {
   if ((p->r - 2) * p->delta + p->q < 32) return SSD_EINVAL;  // Eq. 2-3: every bit of cip in some B(i)
   if (p->k < 1 || p->k > 65534) return SSD_EINVAL;            // Sec. 3.2: k < 65535
   if (p->theta < 1) return SSD_EINVAL;
-  if (p->flags & ~(SSD_VERIFY_H0 | SSD_NO_PRUNE)) return SSD_EINVAL;
+  if (p->flags & ~(SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED)) return SSD_EINVAL;
   if (p->ctb_capacity > (1ull << 32) || p->out_capacity > (1ull << 28)) return SSD_EINVAL;
   uint32_t thr;
   return threshold_of(1u << p->log2_eta, p->theta, &thr);
@@ -287,6 +288,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
       {(void**)&c->n_out, 8},
   };
   for (auto& a : allocs) {
+    if (a.bytes == 0) continue;
     if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       free_ctx(c);
@@ -534,6 +536,67 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   return SSD_OK;
 }
 
+// The fused slot of one router (eta >= 256) in chunks on one stream: chunk 0's
+// touch bits are collected by one launch, then each chunk's streaming kernel
+// applies its bits and, between estimators, collects the next chunk's bits.
+static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs, uint64_t n_pairs,
+                        ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out,
+                        void* stream, uint64_t count, uint64_t n_chunks) {
+  const ssd::Dims& d = ctx->d;
+  const uint64_t n_se = (uint64_t)d.r << d.q;
+  ssd::ScanBatch b;
+  std::memset(&b, 0, sizeof(b));
+  b.n = 1;
+  uint64_t nvec = 0;
+  int rc = add_job(b, 0, router->dr, pairs, n_pairs, &nvec);
+  if (rc != SSD_OK) return rc;
+  b.prefix[1] = nvec;
+  uint64_t tgrid = (nvec + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
+  if (tgrid > (uint64_t)ctx->sms * 8) tgrid = (uint64_t)ctx->sms * 8;
+  if (tgrid < 1) tgrid = 1;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
+  rc = trace(ctx, ctx->tr_start, st);
+  if (rc != SSD_OK) return rc;
+  const uint64_t cnt0 = n_se < count ? n_se : count;
+  cudaError_t e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[0], 0, cnt0, (int)tgrid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
+  ctx->launches += 1;
+  ssd::ChunkArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.router = router->dr;
+  a.global = global ? global->dr : nullptr;
+  a.vec = b.vec[0];
+  a.nvec = nvec;
+  a.edge[0] = b.edge[0];
+  a.edge[1] = b.edge[1];
+  for (uint64_t c = 0; c < n_chunks; ++c) {
+    a.se0 = c * count;
+    a.count = n_se - a.se0 < count ? n_se - a.se0 : count;
+    a.touch = reinterpret_cast<uint8_t*>(ctx->touch[c & 1]);
+    if (c + 1 < n_chunks) {
+      a.next = ctx->touch[(c + 1) & 1];
+      a.nx_se0 = (c + 1) * count;
+      a.nx_count = n_se - a.nx_se0 < count ? n_se - a.nx_se0 : count;
+    } else {
+      a.next = nullptr;
+      a.nx_se0 = a.nx_count = 0;
+    }
+    e = ssd::launch_chunk(d, ctx->s, a, ctx->sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "chunk kernel");
+    ctx->launches += 1;
+  }
+  rc = trace(ctx, ctx->tr_pass, st);
+  unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
+  if (rc != SSD_OK) return rc;
+  if (global) global->slot = router->slot;
+  router->slot += 1;
+  return SSD_OK;
+}
+
 int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs, const uint64_t* n_pairs,
              int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out,
              void* stream) {
@@ -553,6 +616,10 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   uint64_t count = 1;
   while (count * 2 * se_bytes <= ctx->touch_bytes && count * 2 <= pow2_at_least(n_se)) count *= 2;
   const uint64_t n_chunks = (n_se + count - 1) / count;
+  if (n == 1 && d.eta >= 256 && !(d.flags & SSD_SLOT_CHUNKED) && count * se_bytes <= ctx->touch_bytes &&
+      count >= 8 && n_chunks <= 32)
+    return slot_chunks1(ctx, routers[0], d_pairs[0], n_pairs[0], global, d_ips, d_rk, cap, d_n_out, stream, count,
+                        n_chunks);
   if (count * se_bytes > ctx->touch_bytes || count < 8 || n_chunks > 16) {
     int rc = ssd_scan_batch(routers, d_pairs, n_pairs, n, stream);
     if (rc != SSD_OK) return rc;

@@ -88,6 +88,53 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
 cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
                          uint64_t se_count, int grid, cudaStream_t st);
 
+// ---- device helpers shared by the scan and streaming kernels ----
+// Simple tabulation: four 256-word tables indexed by the bytes of x, XORed.
+__device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
+  return T[x & 255u] ^ T[256u + ((x >> 8) & 255u)] ^ T[512u + ((x >> 16) & 255u)] ^ T[768u + (x >> 24)];
+}
+
+// Algorithm 2 for the estimators [se0, se0 + count) only (one chunk, inside one
+// row or whole rows): the recorder a pair sets to 0 is marked in `bits` instead
+// (router base jbase = router * count; estimator se0 + e, recorder x -> bit
+// (jbase + e) * eta + x). sT holds both table sets (2048 words).
+__device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint32_t cip, uint32_t oip,
+                                           const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
+                                           uint64_t se0, uint64_t count) {
+  const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
+  uint32_t x = 0xFFFFFFFFu;
+  for (uint32_t i = r0; i <= r1; ++i) {
+    uint32_t col = c0;
+    if (i) {
+      const uint32_t sh = (i - 1u) * d.delta;
+      col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
+    }
+    const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
+    if (e < count) {
+      if (x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
+      const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
+      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
+    }
+  }
+}
+
+// ---- one chunk of the fused slot of one router (ssd_stream.cu) ----
+// The streaming pass over estimators [se0, se0 + count) with that chunk's touch
+// bits applied; when `next` is set the same kernel collects the touch bits of the
+// next chunk [nx_se0, nx_se0 + nx_count) from the slot's pairs.
+struct ChunkArgs {
+  uint16_t* router;
+  uint16_t* global;          // merged output, or nullptr
+  uint64_t se0, count;
+  uint8_t* touch;            // this chunk's touch bits (cleared as they are applied)
+  uint32_t* next;            // next chunk's touch bits, or nullptr
+  uint64_t nx_se0, nx_count;
+  const uint4* vec;          // the slot's pairs: 16-byte body, nvec vectors of 2 pairs
+  uint64_t nvec;
+  const uint32_t* edge[2];   // head / tail pair outside the body, or nullptr
+};
+cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st);
+
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,

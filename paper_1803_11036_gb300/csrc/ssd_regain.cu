@@ -33,7 +33,7 @@ __device__ __forceinline__ unsigned long long warp_append(bool ok, unsigned long
   return ok ? base + __popc(mask & ((1u << lane) - 1u)) : ~0ull;
 }
 
-__device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
+__device__ __forceinline__ uint32_t tab_hash_global(const uint32_t* T, uint32_t x) {
   return __ldg(T + (x & 255u)) ^ __ldg(T + 256u + ((x >> 8) & 255u)) ^ __ldg(T + 512u + ((x >> 16) & 255u)) ^
          __ldg(T + 768u + (x >> 24));
 }
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
         for (uint32_t j = 0; j < i; ++j) he[j] = s.pool_col[(uint64_t)j * cap + tup[j]];
         he[i] = s.pool_col[(uint64_t)i * cap + idx];
         acc = regain_host(d, he, &cip);
-        if (acc && verify) acc = (tab_hash(s.tables + 1024, cip) & d.col_mask) == he[0];
+        if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
       }
       const unsigned long long pos = warp_append(acc, &s.counters->raw);
       if (acc) {

@@ -10,10 +10,6 @@
 namespace ssd {
 namespace {
 
-__device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
-  return T[x & 255u] ^ T[256u + ((x >> 8) & 255u)] ^ T[512u + ((x >> 16) & 255u)] ^ T[768u + (x >> 24)];
-}
-
 // Algorithm 2 for one pair: DRidx = H1(oip); RHFG[0](cip) from the second table
 // set; RHFG[i](cip) = ((cip >> (i-1)*delta) ^ RHFG[0](cip)) mod 2^q for i >= 1.
 __device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t cip, uint32_t oip,
@@ -99,30 +95,6 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
       const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
       scan_pair(b.dr[j], w.x, w.y, sT, d);
       scan_pair(b.dr[j], w.z, w.w, sT, d);
-    }
-  }
-}
-
-// Algorithm 2 for the estimators [se0, se0 + count) of one chunk: the recorder a
-// pair sets to 0 is marked in `bits` instead (router j, estimator se0 + e,
-// recorder x -> bit (j * count + e) * eta + x). The chunk lies in one row or
-// covers whole rows, so a pair has at most one touch per row of the chunk.
-__device__ __forceinline__ void touch_pair(uint32_t* __restrict__ bits, uint64_t jbase, uint32_t cip, uint32_t oip,
-                                           const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
-                                           uint64_t se0, uint64_t count) {
-  const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
-  uint32_t x = 0xFFFFFFFFu;
-  for (uint32_t i = r0; i <= r1; ++i) {
-    uint32_t col = c0;
-    if (i) {
-      const uint32_t sh = (i - 1u) * d.delta;
-      col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
-    }
-    const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    if (e < count) {
-      if (x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
-      const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
-      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
     }
   }
 }

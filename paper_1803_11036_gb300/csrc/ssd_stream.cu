@@ -59,6 +59,73 @@ __device__ __forceinline__ uint32_t take_touch(uint8_t* p) {
   return t;
 }
 
+// One estimator of one router, all eta recorders (eta >= 256): optional touch
+// bits applied (tb: this lane's byte of the estimator's touch bits), merged
+// value written to g, "< k" bits to `my` (shared) and counted, recorders
+// advanced. Returns the lane's count of recorders below k.
+template <bool ADV, bool HOT, bool TOUCH>
+__device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint4* g, uint64_t base, uint8_t* tb,
+                                                  uint8_t* my, int lane) {
+  const uint32_t iters = d.eta >> 8;
+  const uint32_t kk = d.k | (d.k << 16);
+  uint32_t cnt = 0;
+  for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
+    const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
+    uint4 v[8];
+    uint32_t t[8];
+    // all loads first (a store in between could alias the next load and serialise them)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < (int)m) {
+        v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
+        if (TOUCH) t[u] = tb[(it0 + u) * 32];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < (int)m) {
+        const uint64_t at = base + (it0 + u) * 32 + lane;
+        if (TOUCH) {
+          v[u] = apply8(v[u], t[u]);
+          if (t[u]) tb[(it0 + u) * 32] = 0;
+        }
+        if (g) __stcs(g + at, v[u]);
+        if (HOT) {
+          const uint32_t bits = lt8(v[u], kk);
+          cnt += __popc(bits);
+          my[(it0 + u) * 32 + lane] = (uint8_t)bits;
+        }
+        if (ADV) __stcs(r0 + at, inc8(v[u]));
+      }
+    }
+  }
+  return cnt;
+}
+
+// Pool estimator se when its warp-wide count reaches the threshold (bitmap from `my`).
+__device__ __forceinline__ void pool_if_hot(const Dims& d, const Scratch& s, uint64_t se, uint32_t cnt,
+                                            const uint8_t* my, int lane) {
+  cnt = __reduce_add_sync(kFull, cnt);
+  const uint32_t row = (uint32_t)(se >> d.q), col = (uint32_t)se & d.col_mask;
+  uint32_t idx = kNone;
+  if (cnt >= d.thr) {  // warp-uniform
+    if (lane == 0) idx = pool_slot(d, s, row);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx != kNone) {
+      __syncwarp();
+      const uint32_t* mw = reinterpret_cast<const uint32_t*>(my);
+      uint32_t* dst = s.pool_bm + ((uint64_t)row * d.hse_cap + idx) * d.words;
+      for (uint32_t w = lane; w < d.words; w += 32) dst[w] = mw[w];
+      if (lane == 0) {
+        s.pool_col[(uint64_t)row * d.hse_cap + idx] = col;
+        s.pool_rk[(uint64_t)row * d.hse_cap + idx] = cnt;
+      }
+    }
+  }
+  if (lane == 0) s.hot_idx[se] = idx;
+  __syncwarp();
+}
+
 // eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
 template <bool ONE, bool ADV, bool HOT, bool TOUCH>
 __global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const Scratch s,
@@ -79,37 +146,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const 
     uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane : nullptr;
     uint32_t cnt = 0;
     if (ONE) {
-      uint4* const r0 = reinterpret_cast<uint4*>(a.routers[0]);
-      for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
-        const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
-        uint4 v[8];
-        uint32_t t[8];
-        // all loads first (a store in between could alias the next load and serialise them)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (u < (int)m) {
-            v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
-            if (TOUCH) t[u] = tb[(it0 + u) * 32];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (u < (int)m) {
-            const uint64_t at = base + (it0 + u) * 32 + lane;
-            if (TOUCH) {
-              v[u] = apply8(v[u], t[u]);
-              if (t[u]) tb[(it0 + u) * 32] = 0;
-            }
-            if (g) __stcs(g + at, v[u]);
-            if (HOT) {
-              const uint32_t bits = lt8(v[u], kk);
-              cnt += __popc(bits);
-              my[(it0 + u) * 32 + lane] = (uint8_t)bits;
-            }
-            if (ADV) __stcs(r0 + at, inc8(v[u]));
-          }
-        }
-      }
+      cnt = one_router_se<ADV, HOT, TOUCH>(d, reinterpret_cast<uint4*>(a.routers[0]), g, base, tb, my, lane);
     } else {
       for (uint32_t it = 0; it < iters; ++it) {
         const uint64_t at = base + it * 32 + lane;
@@ -132,27 +169,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const 
         }
       }
     }
-    if (HOT) {
-      cnt = __reduce_add_sync(kFull, cnt);
-      const uint32_t row = (uint32_t)(se >> d.q), col = (uint32_t)se & d.col_mask;
-      uint32_t idx = kNone;
-      if (cnt >= d.thr) {  // warp-uniform
-        if (lane == 0) idx = pool_slot(d, s, row);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx != kNone) {
-          __syncwarp();
-          const uint32_t* mw = reinterpret_cast<const uint32_t*>(my);
-          uint32_t* dst = s.pool_bm + ((uint64_t)row * d.hse_cap + idx) * d.words;
-          for (uint32_t w = lane; w < d.words; w += 32) dst[w] = mw[w];
-          if (lane == 0) {
-            s.pool_col[(uint64_t)row * d.hse_cap + idx] = col;
-            s.pool_rk[(uint64_t)row * d.hse_cap + idx] = cnt;
-          }
-        }
-      }
-      if (lane == 0) s.hot_idx[se] = idx;
-      __syncwarp();
-    }
+    if (HOT) pool_if_hot(d, s, se, cnt, my, lane);
   }
 }
 
@@ -212,6 +229,53 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
   }
 }
 
+// One chunk of the fused slot of one router (eta >= 256): each warp streams
+// estimators of the chunk with their touch bits applied, counts and pools hot
+// ones and advances; with NEXT, between estimators each lane also hashes a share
+// of the slot's pairs and sets the touch bits of the next chunk (L2 atomics that
+// fill the gaps of the memory-bound stream).
+template <bool NEXT>
+__global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s, const __grid_constant__ ChunkArgs a) {
+  extern __shared__ __align__(16) uint32_t smc[];
+  uint32_t* sT = smc;                                              // 2048 table words (NEXT)
+  uint8_t* masks = reinterpret_cast<uint8_t*>(smc + (NEXT ? 2048 : 0));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* my = masks + (size_t)wid * (d.eta >> 3);
+  if (NEXT) {
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = s.tables[i];
+    __syncthreads();
+  }
+  const uint32_t nr0 = NEXT ? (uint32_t)(a.nx_se0 >> d.q) : 0u;
+  const uint32_t nr1 = NEXT ? (uint32_t)((a.nx_se0 + a.nx_count - 1) >> d.q) : 0u;
+  const uint64_t slots = a.count * 32;   // (estimator, lane) slots sharing the pairs
+  uint4* const r0 = reinterpret_cast<uint4*>(a.router);
+  uint4* const g = reinterpret_cast<uint4*>(a.global);
+  const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
+    const uint64_t se = a.se0 + e;
+    uint8_t* tb = a.touch + e * (d.eta >> 3) + lane;
+    // this slot's first pair vector is loaded before the estimator so the two loads overlap
+    uint64_t v = e * 32 + lane;
+    uint4 w0 = make_uint4(0, 0, 0, 0);
+    if (NEXT && v < a.nvec) w0 = __ldcs(a.vec + v);
+    const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, tb, my, lane);
+    if (NEXT) {
+      if (v < a.nvec) {
+        touch_pair(a.next, 0, w0.x, w0.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        touch_pair(a.next, 0, w0.z, w0.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      }
+      for (v += slots; v < a.nvec; v += slots) {
+        const uint4 w = __ldcs(a.vec + v);
+        touch_pair(a.next, 0, w.x, w.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        touch_pair(a.next, 0, w.z, w.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      }
+      if (e == 0 && lane < 2 && a.edge[lane])
+        touch_pair(a.next, 0, a.edge[lane][0], a.edge[lane][1], sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+    }
+    pool_if_hot(d, s, se, cnt, my, lane);
+  }
+}
+
 template <typename K>
 int blocks_per_sm(K kernel, size_t smem, int spare) {
   int b = 0;
@@ -260,6 +324,22 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
   SSD_STREAM_CASE(false, true, true, true)
 #undef SSD_STREAM_CASE
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
+  const size_t masks = (size_t)(kBlock / 32) * (d.eta >> 3);
+  uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
+  if (a.next) {
+    const size_t smem = masks + 2048 * 4;
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<true>, smem, 0);
+    if (grid > need) grid = need;
+    k_chunk<true><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+  } else {
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<false>, masks, 0);
+    if (grid > need) grid = need;
+    k_chunk<false><<<(unsigned)grid, kBlock, masks, st>>>(d, s, a);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace ssd

@@ -206,21 +206,29 @@ def test_slots_fused_close(wl, with_global):
     run.close()
 
 
-@pytest.mark.parametrize("wl,chunk,with_global", [
-    ("tiny", 0, True),                      # one chunk, eta = 64 (small-estimator kernel)
-    ("tiny", 4096, True),                   # five chunks of one row
-    ("tiny", 1024, False),                  # too many chunks: scan_batch + close_slot
-    ("paper_c1", 0, False),                 # one chunk holding all rows
-    ("paper_c1", 2 << 20, True),            # ten chunks, two per row
-    ("paper_c1", 10 << 20, False),          # three chunks of two rows, the last one partial
-    ("edge_small", 0, True),                # four routers
-    ("stress_small", 16 << 20, False),      # eight routers, hot sources, ten chunks
-    ("stress_small", 64 << 10, False),      # eight routers, fallback
+CH = ssd.SSD_SLOT_CHUNKED
+
+
+@pytest.mark.parametrize("wl,chunk,flags,with_global", [
+    ("tiny", 0, 0, True),                   # one chunk, eta = 64 (small-estimator kernel)
+    ("tiny", 4096, 0, True),                # five chunks of one row
+    ("tiny", 1024, 0, False),               # too many chunks: scan_batch + close_slot
+    ("paper_c1", 0, 0, False),              # one router: one chunk, no next-chunk collection
+    ("paper_c1", 2 << 20, 0, True),         # one router: ten chunks, each collecting the next
+    ("paper_c1", 10 << 20, 0, False),       # one router: three chunks, the last one partial
+    ("corelink_small", 4 << 20, 0, False),
+    ("paper_c1", 0, CH, False),             # chunked: one chunk holding all rows
+    ("paper_c1", 2 << 20, CH, True),        # ten chunks, two per row
+    ("paper_c1", 10 << 20, CH, False),      # three chunks of two rows, the last one partial
+    ("edge_small", 0, 0, True),             # four routers
+    ("stress_small", 16 << 20, 0, False),   # eight routers, hot sources, ten chunks
+    ("stress_small", 64 << 10, 0, False),   # eight routers, fallback
 ])
-def test_fused_slot(wl, chunk, with_global):
-    """ssd_slot (touch bits in L2, applied by the streaming pass) gives the oracle's list and
-    merged sketch every slot, and leaves the routers the oracle holds advanced by one."""
-    run = Run(wl, touch_chunk_bytes=chunk)
+def test_fused_slot(wl, chunk, flags, with_global):
+    """ssd_slot (the scan's touches applied by the streaming pass, from L2 bits or from binned
+    records) gives the oracle's list and merged sketch every slot, and leaves the routers the
+    oracle holds advanced by one."""
+    run = Run(wl, flags, touch_chunk_bytes=chunk)
     for _ in range(run.W["slots"]):
         got, want = run.step_slot("pruned", with_global=with_global)
         assert_list_equal(got, want, f"{wl} slot {run.t}")
@@ -231,6 +239,28 @@ def test_fused_slot(wl, chunk, with_global):
         oracle.advance(run.p, nxt)
         assert np.array_equal(r_gpu.export(), nxt)
     run.close()
+
+
+@pytest.mark.parametrize("flags", [0, CH])
+@pytest.mark.parametrize("n", [0, 1, 3, 4097, (1 << 18) + 5])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_slot_ragged(n, offset, flags):
+    """The one-router routes (chunks collecting the next chunk's bits; bits collected on the side
+    stream) on empty, odd and unaligned pair buffers: the router they leave is the oracle's after
+    scan + advance, and the list is the oracle's."""
+    W = tg.workload("paper_c1")
+    p, tabs, ctx = setup(W, flags, touch_chunk_bytes=2 << 20)
+    pairs = tg.traffic_for(W).fill(0, n=n + 2)
+    dev = to_dev(pairs)[2 * offset: 2 * (offset + n)]
+    sk = ctx.sketch()
+    got = ctx.slot([sk], [dev])
+    want_sk = oracle.new_sketch(p)
+    oracle.scan(p, tabs, want_sk, pairs[offset:offset + n])
+    want = oracle.regain(p, tabs, want_sk, "pruned")
+    assert np.array_equal(got[0], want["ips"]) and np.array_equal(got[1], want["rk"])
+    oracle.advance(p, want_sk)
+    assert np.array_equal(sk.export(), want_sk)
+    ctx.close()
 
 
 @pytest.mark.parametrize("wl,pinned", [("edge_small", False), ("paper_c1", True)])
