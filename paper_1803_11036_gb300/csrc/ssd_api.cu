@@ -35,6 +35,9 @@ struct ssd_ctx {
   uint64_t touch_bytes;
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_touched[2], ev_closed[2];
+  // pre-hashed pairs of the one-router fused slot (grown to the largest slot)
+  uint2* packed;
+  uint64_t packed_cap;
   // host-pair staging of ssd_slot_host (double-buffered, sized to the largest slot)
   uint32_t* hs_buf[2];
   uint64_t hs_bytes;
@@ -186,6 +189,7 @@ void free_ctx(ssd_ctx* c) {
     if (c->ev_hs_free[i]) cudaEventDestroy(c->ev_hs_free[i]);
     cudaFree(c->hs_buf[i]);
   }
+  cudaFree(c->packed);
 
   cudaFree(c->tables);
   cudaFree(c->hot_idx);
@@ -556,21 +560,51 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   if (tgrid < 1) tgrid = 1;
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
+  // both hashes of every pair once per slot when they pack into one word
+  const bool prehash = d.q + d.log2_eta <= 32;
+  if (prehash && n_pairs > ctx->packed_cap) {  // a larger slot than any before: grow (waits for `stream`)
+    SSD_CUDA(cudaStreamSynchronize(st));
+    cudaFree(ctx->packed);
+    ctx->packed = nullptr;
+    const uint64_t want = n_pairs + n_pairs / 4 + 64;
+    if (cudaMalloc(&ctx->packed, want * 8) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->packed_cap = 0;
+      return SSD_ENOMEM;
+    }
+    ctx->packed_cap = want;
+  }
   SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
   rc = trace(ctx, ctx->tr_start, st);
   if (rc != SSD_OK) return rc;
   const uint64_t cnt0 = n_se < count ? n_se : count;
-  cudaError_t e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[0], 0, cnt0, (int)tgrid, st);
-  if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
-  ctx->launches += 1;
   ssd::ChunkArgs a;
   std::memset(&a, 0, sizeof(a));
   a.router = router->dr;
   a.global = global ? global->dr : nullptr;
-  a.vec = b.vec[0];
-  a.nvec = nvec;
-  a.edge[0] = b.edge[0];
-  a.edge[1] = b.edge[1];
+  cudaError_t e;
+  if (prehash) {
+    if (n_pairs) {
+      e = ssd::launch_prehash(d, ctx->tables, b, ctx->packed, (int)tgrid, st);
+      if (e != cudaSuccess) return cuda_fail(e, "prehash kernel");
+      ctx->launches += 1;
+    }
+    a.packed = 1;
+    a.vec = reinterpret_cast<const uint4*>(ctx->packed);
+    a.nvec = n_pairs / 2;
+    a.edge[0] = (n_pairs & 1) ? reinterpret_cast<const uint32_t*>(ctx->packed + (n_pairs - 1)) : nullptr;
+    a.edge[1] = nullptr;
+    e = ssd::launch_touch_packed(d, a.vec, a.nvec, reinterpret_cast<const uint2*>(a.edge[0]), ctx->touch[0], 0,
+                                 cnt0, (int)tgrid, st);
+  } else {
+    a.vec = b.vec[0];
+    a.nvec = nvec;
+    a.edge[0] = b.edge[0];
+    a.edge[1] = b.edge[1];
+    e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[0], 0, cnt0, (int)tgrid, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
+  ctx->launches += 1;
   for (uint64_t c = 0; c < n_chunks; ++c) {
     a.se0 = c * count;
     a.count = n_se - a.se0 < count ? n_se - a.se0 : count;

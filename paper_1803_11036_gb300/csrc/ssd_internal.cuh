@@ -118,6 +118,36 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
   }
 }
 
+// touch_pair on a pre-hashed pair: packed = RHFG[0](cip) | H1(oip) << q (q + log2_eta <= 32).
+__device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint32_t packed, const Dims& d,
+                                             uint32_t r0, uint32_t r1, uint64_t se0, uint64_t count) {
+  const uint32_t c0 = packed & d.col_mask;
+  const uint32_t x = packed >> d.q;
+  for (uint32_t i = r0; i <= r1; ++i) {
+    uint32_t col = c0;
+    if (i) {
+      const uint32_t sh = (i - 1u) * d.delta;
+      col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
+    }
+    const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
+    if (e < count) {
+      const uint64_t bit = (e << d.log2_eta) | x;
+      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
+    }
+  }
+}
+
+// ---- per-slot pre-hash of one router's pairs (ssd_scan.cu) ----
+// out[m] = (cip, RHFG[0](cip) | H1(oip) << q) for every pair of the buffer described by
+// job 0 of b: the body vectors first (out[2v], out[2v+1]), then the head and tail pairs.
+// The result holds n_pairs entries in an order the order-free scan does not see.
+cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint2* out, int grid,
+                           cudaStream_t st);
+// Algorithm 2 for one chunk from pre-hashed pairs (one router): `vec` holds nvec
+// vectors of two packed pairs, `tail` one more packed pair or nullptr.
+cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
+                                uint64_t se0, uint64_t se_count, int grid, cudaStream_t st);
+
 // ---- one chunk of the fused slot of one router (ssd_stream.cu) ----
 // The streaming pass over estimators [se0, se0 + count) with that chunk's touch
 // bits applied; when `next` is set the same kernel collects the touch bits of the
@@ -132,6 +162,7 @@ struct ChunkArgs {
   const uint4* vec;          // the slot's pairs: 16-byte body, nvec vectors of 2 pairs
   uint64_t nvec;
   const uint32_t* edge[2];   // head / tail pair outside the body, or nullptr
+  int packed;                // vec/edge[0] hold pre-hashed pairs (edge[1] unused)
 };
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st);
 

@@ -137,7 +137,68 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
   }
 }
 
+// Both hashes of every pair once per slot: packed = RHFG[0](cip) | H1(oip) << q.
+__global__ void __launch_bounds__(kBlock) k_prehash(const Dims d, const uint32_t* __restrict__ tables,
+                                                    const __grid_constant__ ScanBatch b, uint2* __restrict__ out) {
+  __shared__ uint32_t sT[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
+  __syncthreads();
+  const uint64_t nvec = b.prefix[1];
+  auto pack = [&](uint32_t cip, uint32_t oip) {
+    return make_uint2(cip, (tab_hash(sT + 1024, cip) & d.col_mask) | ((tab_hash(sT, oip) & (d.eta - 1u)) << d.q));
+  };
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const uint4 w = __ldcs(b.vec[0] + v);
+    const uint2 p0 = pack(w.x, w.y), p1 = pack(w.z, w.w);
+    reinterpret_cast<uint4*>(out)[v] = make_uint4(p0.x, p0.y, p1.x, p1.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint64_t at = 2 * nvec;
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t* e = b.edge[k];
+      if (e) out[at++] = pack(e[0], e[1]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_touch_packed(const Dims d, const uint4* __restrict__ vec, uint64_t nvec,
+                                                         const uint2* __restrict__ tail, uint32_t* __restrict__ bits,
+                                                         uint64_t se0, uint64_t count) {
+  const uint32_t r0 = (uint32_t)(se0 >> d.q), r1 = (uint32_t)((se0 + count - 1) >> d.q);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && tail) touch_packed(bits, tail->x, tail->y, d, r0, r1, se0, count);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; v + (kUnroll - 1) * stride < nvec; v += kUnroll * stride) {
+    uint4 w[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) w[u] = __ldcs(vec + v + u * stride);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      touch_packed(bits, w[u].x, w[u].y, d, r0, r1, se0, count);
+      touch_packed(bits, w[u].z, w[u].w, d, r0, r1, se0, count);
+    }
+  }
+  for (; v < nvec; v += stride) {
+    const uint4 w = __ldcs(vec + v);
+    touch_packed(bits, w.x, w.y, d, r0, r1, se0, count);
+    touch_packed(bits, w.z, w.w, d, r0, r1, se0, count);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint2* out, int grid,
+                           cudaStream_t st) {
+  k_prehash<<<grid, kBlock, 0, st>>>(d, tables, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
+                                uint64_t se0, uint64_t se_count, int grid, cudaStream_t st) {
+  k_touch_packed<<<grid, kBlock, 0, st>>>(d, vec, nvec, tail, bits, se0, se_count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
                          uint64_t se_count, int grid, cudaStream_t st) {

@@ -234,14 +234,16 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
 // ones and advances; with NEXT, between estimators each lane also hashes a share
 // of the slot's pairs and sets the touch bits of the next chunk (L2 atomics that
 // fill the gaps of the memory-bound stream).
-template <bool NEXT>
-__global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s, const __grid_constant__ ChunkArgs a) {
+template <bool NEXT, bool PACKED>
+__global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s,
+                                                              const __grid_constant__ ChunkArgs a) {
+  constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
   extern __shared__ __align__(16) uint32_t smc[];
-  uint32_t* sT = smc;                                              // 2048 table words (NEXT)
-  uint8_t* masks = reinterpret_cast<uint8_t*>(smc + (NEXT ? 2048 : 0));
+  uint32_t* sT = smc;                                              // 2048 table words
+  uint8_t* masks = reinterpret_cast<uint8_t*>(smc + (TABLES ? 2048 : 0));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* my = masks + (size_t)wid * (d.eta >> 3);
-  if (NEXT) {
+  if (TABLES) {
     for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = s.tables[i];
     __syncthreads();
   }
@@ -251,6 +253,15 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
   uint4* const r0 = reinterpret_cast<uint4*>(a.router);
   uint4* const g = reinterpret_cast<uint4*>(a.global);
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
+  auto touch2 = [&](uint4 w) {
+    if (PACKED) {
+      touch_packed(a.next, w.x, w.y, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_packed(a.next, w.z, w.w, d, nr0, nr1, a.nx_se0, a.nx_count);
+    } else {
+      touch_pair(a.next, 0, w.x, w.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair(a.next, 0, w.z, w.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+    }
+  };
   for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
     const uint64_t se = a.se0 + e;
     uint8_t* tb = a.touch + e * (d.eta >> 3) + lane;
@@ -260,17 +271,13 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
     if (NEXT && v < a.nvec) w0 = __ldcs(a.vec + v);
     const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, tb, my, lane);
     if (NEXT) {
-      if (v < a.nvec) {
-        touch_pair(a.next, 0, w0.x, w0.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-        touch_pair(a.next, 0, w0.z, w0.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      if (v < a.nvec) touch2(w0);
+      for (v += slots; v < a.nvec; v += slots) touch2(__ldcs(a.vec + v));
+      if (e == 0 && lane < 2 && a.edge[lane]) {
+        const uint32_t* p = a.edge[lane];
+        if (PACKED) touch_packed(a.next, p[0], p[1], d, nr0, nr1, a.nx_se0, a.nx_count);
+        else touch_pair(a.next, 0, p[0], p[1], sT, d, nr0, nr1, a.nx_se0, a.nx_count);
       }
-      for (v += slots; v < a.nvec; v += slots) {
-        const uint4 w = __ldcs(a.vec + v);
-        touch_pair(a.next, 0, w.x, w.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-        touch_pair(a.next, 0, w.z, w.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-      }
-      if (e == 0 && lane < 2 && a.edge[lane])
-        touch_pair(a.next, 0, a.edge[lane][0], a.edge[lane][1], sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
     pool_if_hot(d, s, se, cnt, my, lane);
   }
@@ -326,20 +333,20 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
-  const size_t masks = (size_t)(kBlock / 32) * (d.eta >> 3);
-  uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
-  if (a.next) {
-    const size_t smem = masks + 2048 * 4;
-    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<true>, smem, 0);
-    if (grid > need) grid = need;
-    k_chunk<true><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
-  } else {
-    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<false>, masks, 0);
-    if (grid > need) grid = need;
-    k_chunk<false><<<(unsigned)grid, kBlock, masks, st>>>(d, s, a);
-  }
+template <bool NEXT, bool PACKED>
+cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)(kBlock / 32) * (d.eta >> 3) + (NEXT && !PACKED ? 2048 * 4 : 0);
+  const uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED>, smem, 0);
+  if (grid > need) grid = need;
+  k_chunk<NEXT, PACKED><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
+  if (!a.next) return launch_chunk_variant<false, false>(d, s, a, sms, st);
+  if (a.packed) return launch_chunk_variant<true, true>(d, s, a, sms, st);
+  return launch_chunk_variant<true, false>(d, s, a, sms, st);
 }
 
 }  // namespace ssd
