@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--touch-chunk-mib", type=int, default=0, help="touch bits per chunk of the fused slot")
     return ap.parse_args()
 
@@ -478,6 +479,30 @@ def run_ours(args, world, rank, local):
     scan_mpps = timed_pk / (scan_ms * args.steps / 1e3) / 1e6
     del scratch
 
+    # ---- the same slots replayed from one captured CUDA graph (fixed-size slots only)
+    graph_leg = None
+    counts = [x.numel() // 2 for x in slot_dev[0]]
+    if not args.no_graph and all([x.numel() // 2 for x in s] == counts for s in slot_dev):
+        g = ssd.SlotGraph(ctx, routers, counts, None, cap=cap)
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for dst, src in zip(g.inputs, slot_dev[fill]):
+                dst.copy_(src)
+            g.replay()                       # warm-up
+            ga.record(stream)
+            for i in range(args.steps):
+                for dst, src in zip(g.inputs, slot_dev[fill + args.warmup + i]):
+                    dst.copy_(src)
+                g.replay()
+            gb.record(stream)
+        stream.synchronize()
+        graph_ms = ga.elapsed_time(gb) / args.steps
+        graph_leg = {"replay_ms_per_slot": round(graph_ms, 4), "direct_ms_per_slot": round(total_ms / args.steps, 4),
+                     "mpps": round(timed_pk / (graph_ms * args.steps / 1e3) / 1e6, 1),
+                     "note": "one captured ssd_slot replayed per slot; the time includes copying the slot's "
+                             "pairs into the graph's input buffers"}
+        del g
+
     eta, C, r = 1 << prm["log2_eta"], 1 << prm["q"], prm["r"]
     recorders = eta * C * r
     pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
@@ -577,6 +602,7 @@ def run_ours(args, world, rank, local):
                     "candidates_and_list": round(statistics.mean(tail_ms), 4),
                     "total": round(max_ms / args.steps, 4)},
         "reconstruct_ms_per_slice": round(statistics.mean(tail_ms), 4),
+        "cuda_graph": graph_leg,
         "batched_vs_plain": bvp,
         "served": served,
         "roofline": {"kernel": "k_chunk (one router: the scan's touches applied, hot extraction, advance; the next "

@@ -136,6 +136,9 @@ SSD_API void ssd_sketch_destroy(ssd_sketch* s);
 SSD_API uint64_t ssd_sketch_bytes(const ssd_ctx* ctx);
 /* Slots the sketch has advanced since creation or import. */
 SSD_API int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot);
+/* Set the slot counter (host bookkeeping only, no GPU work): after replaying a
+ * captured slot the caller advances the counters the replay cannot. */
+SSD_API int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot);
 /* Copy `count` recorders starting at recorder `first` to dst (host or device).
  * Waits for `stream` before returning. Checkpointing a sketch is
  * export + ssd_sketch_slot; resuming is import. */
@@ -267,6 +270,13 @@ SSD_API int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* c
 SSD_API int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* h_pairs,
                           const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
                           uint64_t cap, uint64_t* d_n_out, void* stream);
+
+/* Allocate now what ssd_slot and ssd_slot_host would otherwise allocate on a
+ * first call with up to max_pairs pairs in the slot (summed over its routers):
+ * the pre-hashed pairs and the host staging areas. Later calls with at most
+ * that many pairs allocate nothing, so ssd_slot can be captured in a CUDA graph
+ * (stream capture cannot allocate). Waits for the device. */
+SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
 
 /* Counters of the context's last regain or close (waits for `stream`). */
 SSD_API int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream);

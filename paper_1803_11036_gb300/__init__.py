@@ -27,8 +27,8 @@ from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SLOT_CHUNKE
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
                    Params, SSDError, Stats, check, load)
 
-__all__ = ["Context", "Sketch", "SSDError", "SSD_VERIFY_H0", "SSD_NO_PRUNE", "make_params", "threshold",
-           "params_ok", "library_path"]
+__all__ = ["Context", "Sketch", "SlotGraph", "SSDError", "SSD_VERIFY_H0", "SSD_NO_PRUNE", "make_params",
+           "threshold", "params_ok", "library_path"]
 
 
 def library_path() -> str:
@@ -96,6 +96,10 @@ class Sketch:
         v = ctypes.c_uint64()
         check(self.ctx.L.ssd_sketch_slot(self._h, ctypes.byref(v)), "ssd_sketch_slot")
         return v.value
+
+    @slot.setter
+    def slot(self, value: int) -> None:
+        check(self.ctx.L.ssd_sketch_set_slot(self._h, value), "ssd_sketch_set_slot")
 
     def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
         """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""
@@ -320,6 +324,10 @@ class Context:
         m = int(n_out.item())
         return ips[:m].cpu().numpy().view(np.uint32).copy(), rk[:m].cpu().numpy().view(np.uint32).copy()
 
+    def reserve(self, max_pairs: int) -> None:
+        """Allocate what slot()/slot_host() allocate on a first call with up to max_pairs pairs."""
+        check(self.L.ssd_reserve(self._h, max_pairs), "ssd_reserve")
+
     def stats(self, stream=None) -> dict:
         st = Stats()
         check(self.L.ssd_stats_get(self._h, ctypes.byref(st), _stream_handle(stream, self.device)),
@@ -344,3 +352,45 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class SlotGraph:
+    """A whole slot (scan + merge + regain + advance, ``Context.slot``) captured once as a CUDA
+    graph on fixed device buffers. Each replay processes the pairs currently in ``inputs``
+    (router j's buffer holds exactly ``counts[j]`` pairs every slot), writes the list to
+    ``ips``/``rk``/``n_out`` and advances the routers' slot counters as the call would have."""
+
+    def __init__(self, ctx: Context, routers, counts, global_sketch: Sketch | None = None, cap: int = 1 << 16):
+        torch = _torch()
+        self.ctx, self.routers, self.global_sketch = ctx, list(routers), global_sketch
+        self.inputs = [torch.zeros(2 * int(n), dtype=torch.int32, device=ctx.device) for n in counts]
+        self.ips, self.rk = ctx._outputs(cap)
+        self.n_out = torch.zeros(1, dtype=torch.int64, device=ctx.device)
+        ctx.reserve(int(sum(counts)))
+        slots = [r.slot for r in self.routers]
+        gslot = global_sketch.slot if global_sketch is not None else None
+        self.stream = torch.cuda.Stream(ctx.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            ctx.slot(self.routers, self.inputs, global_sketch, out=(self.ips, self.rk, self.n_out),
+                     stream=torch.cuda.current_stream(), sync=False)
+        # capture ran no kernels: put the host counters back
+        for r, v in zip(self.routers, slots):
+            r.slot = v
+        if global_sketch is not None:
+            global_sketch.slot = gslot
+
+    def replay(self) -> None:
+        """Run the captured slot on the current contents of `inputs` (asynchronous)."""
+        merged = self.routers[0].slot
+        self.graph.replay()
+        for r in self.routers:
+            r.slot = r.slot + 1
+        if self.global_sketch is not None:
+            self.global_sketch.slot = merged
+
+    def result(self):
+        """The list of the last replay as host arrays (waits for it)."""
+        m = int(self.n_out.item())
+        return (self.ips[:m].cpu().numpy().view(np.uint32).copy(),
+                self.rk[:m].cpu().numpy().view(np.uint32).copy())

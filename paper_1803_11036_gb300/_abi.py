@@ -46,6 +46,7 @@ SIGNATURES = {
     "ssd_sketch_destroy": ([_vp], None),
     "ssd_sketch_bytes": ([_vp], _u64),
     "ssd_sketch_slot": ([_vp, ctypes.POINTER(_u64)], _int),
+    "ssd_sketch_set_slot": ([_vp, _u64], _int),
     "ssd_sketch_export": ([_vp, _u64, _u64, _vp, _vp], _int),
     "ssd_sketch_import": ([_vp, _vp, _u64, _vp], _int),
     "ssd_scan": ([_vp, _vp, _u64, _vp], _int),
@@ -58,6 +59,7 @@ SIGNATURES = {
     "ssd_close_slot": ([_vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_slot": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_slot_host": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
+    "ssd_reserve": ([_vp, _u64], _int),
     "ssd_set_trace": ([_vp, _vp, _vp, _vp], _int),
     "ssd_stats_get": ([_vp, ctypes.POINTER(Stats), _vp], _int),
     "ssd_launch_count": ([_vp], _u64),

@@ -373,6 +373,12 @@ int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot) {
   return SSD_OK;
 }
 
+int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot) {
+  if (!s) return SSD_EINVAL;
+  s->slot = slot;
+  return SSD_OK;
+}
+
 int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
   if (!s || (count && !dst)) return SSD_EINVAL;
   const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;
@@ -764,6 +770,36 @@ int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* cons
   if (rc != SSD_OK) return rc;
   SSD_CUDA(cudaEventRecord(ctx->ev_hs_free[b], st));
   ctx->hs_calls += 1;
+  return SSD_OK;
+}
+
+int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs) {
+  if (!ctx) return SSD_EINVAL;
+  DeviceGuard g(ctx->device);
+  SSD_CUDA(cudaDeviceSynchronize());
+  if (max_pairs > ctx->packed_cap) {
+    cudaFree(ctx->packed);
+    ctx->packed = nullptr;
+    if (cudaMalloc(&ctx->packed, max_pairs * 8) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->packed_cap = 0;
+      return SSD_ENOMEM;
+    }
+    ctx->packed_cap = max_pairs;
+  }
+  const uint64_t bytes = ((max_pairs * 8 + 15) & ~15ull) + 256;
+  if (bytes > ctx->hs_bytes) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(ctx->hs_buf[i]);
+      ctx->hs_buf[i] = nullptr;
+      if (cudaMalloc(&ctx->hs_buf[i], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hs_bytes = 0;
+        return SSD_ENOMEM;
+      }
+    }
+    ctx->hs_bytes = bytes;
+  }
   return SSD_OK;
 }
 

@@ -1,0 +1,60 @@
+"""Accuracy of the GPU detector against exact ground truth, with the paper's rates (Sec. 5):
+FPR = hosts reported that are not sliding super points / true sliding super points,
+FNR = sliding super points not reported / true sliding super points, TFR = FPR + FNR.
+Ground truth is the precise algorithm (exact distinct opposite hosts per window). The rates
+are printed for the record and held to loose bounds; the paper's own figures come from a
+different trace and are not comparable."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1803_11036_gb300 as ssd
+import trafficgen as tg
+from gpu_harness import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def rates(reported, truth):
+    rep, tru = set(reported.tolist()), set(truth.tolist())
+    if not tru:
+        return None
+    fp = len(rep - tru) / len(tru)
+    fn = len(tru - rep) / len(tru)
+    return fp, fn
+
+
+@pytest.mark.parametrize("wl", ["paper_c1", "corelink_small"])
+def test_fpr_fnr_against_exact_counts(wl):
+    W = tg.workload(wl)
+    prm = W["params"]
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    k = prm["k"]
+    ctxs = {m: ssd.Context(ssd.make_params(prm, f), tabs) for m, f in (("literal", 0), ("verify", ssd.SSD_VERIFY_H0))}
+    sk = {m: c.sketch() for m, c in ctxs.items()}
+    ex = oracle.Exact(k, prm["theta"])
+    per = {m: [] for m in ctxs}
+    for t in range(W["slots"]):
+        pairs = T.slot(t)
+        ex.add_slot(pairs[0])
+        truth, _ = ex.report()
+        dev = to_dev(pairs[0])
+        for m, c in ctxs.items():
+            ips, _ = c.slot([sk[m]], [dev])
+            if t >= k - 1:                      # windows that hold k slots
+                r = rates(ips, truth)
+                if r is not None:
+                    per[m].append(r)
+    out = {}
+    for m, v in per.items():
+        a = np.array(v)
+        out[m] = dict(FPR=float(a[:, 0].mean()), FNR=float(a[:, 1].mean()), TFR=float(a.sum(axis=1).mean()),
+                      windows=len(v))
+    print(f"\n{wl} accuracy over full windows: {out}")
+    # the checked list is a subset of the literal one: fewer false alarms, never fewer misses
+    assert out["verify"]["FPR"] <= out["literal"]["FPR"]
+    assert out["verify"]["FNR"] >= out["literal"]["FNR"] - 1e-12
+    assert out["verify"]["TFR"] < 0.5
+    for c in ctxs.values():
+        c.close()
