@@ -27,8 +27,8 @@ __device__ __forceinline__ uint4 min8(uint4 a, uint4 b) {
 }
 // bit i of the result = (recorder i < k) for the 8 recorders of v
 __device__ __forceinline__ uint32_t lt2(uint32_t w, uint32_t kk) {
-  const uint32_t c = __vcmpltu2(w, kk);
-  return (c & 1u) | ((c >> 15) & 2u);
+  const uint32_t k = kk & 0xFFFFu;
+  return (uint32_t)((w & 0xFFFFu) < k) | ((uint32_t)((w >> 16) < k) << 1);
 }
 __device__ __forceinline__ uint32_t lt8(uint4 v, uint32_t kk) {
   return lt2(v.x, kk) | (lt2(v.y, kk) << 2) | (lt2(v.z, kk) << 4) | (lt2(v.w, kk) << 6);
@@ -85,9 +85,9 @@ __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint
     for (int u = 0; u < 8; ++u) {
       if (u < (int)m) {
         const uint64_t at = base + (it0 + u) * 32 + lane;
-        if (TOUCH) {
+        if (TOUCH && t[u]) {
           v[u] = apply8(v[u], t[u]);
-          if (t[u]) tb[(it0 + u) * 32] = 0;
+          tb[(it0 + u) * 32] = 0;
         }
         if (g) __stcs(g + at, v[u]);
         if (HOT) {
@@ -128,7 +128,7 @@ __device__ __forceinline__ void pool_if_hot(const Dims& d, const Scratch& s, uin
 
 // eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
 template <bool ONE, bool ADV, bool HOT, bool TOUCH>
-__global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const Scratch s,
+__global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) uint8_t smask[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -150,16 +150,30 @@ __global__ void __launch_bounds__(kBlock, 4) k_stream_large(const Dims d, const 
     } else {
       for (uint32_t it = 0; it < iters; ++it) {
         const uint64_t at = base + it * 32 + lane;
-        uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
-        uint4 mv = __ldcs(rp + at);
-        if (TOUCH) mv = apply8(mv, take_touch(tb + it * 32));
-        if (ADV) __stcs(rp + at, inc8(mv));
-        for (int n = 1; n < a.n; ++n) {
-          rp = reinterpret_cast<uint4*>(a.routers[n]);
-          uint4 v = __ldcs(rp + at);
-          if (TOUCH) v = apply8(v, take_touch(tb + n * tstride + it * 32));
-          mv = min8(mv, v);
-          if (ADV) __stcs(rp + at, inc8(v));
+        uint4 mv = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        // routers in groups of 8: the group's loads are issued before any of its stores
+        for (int n0 = 0; n0 < a.n; n0 += 8) {
+          const int m = a.n - n0 < 8 ? a.n - n0 : 8;
+          uint4 v[8];
+          uint32_t t[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u < m) {
+              v[u] = __ldcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at);
+              if (TOUCH) t[u] = tb[(uint64_t)(n0 + u) * tstride + it * 32];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u < m) {
+              if (TOUCH && t[u]) {
+                v[u] = apply8(v[u], t[u]);
+                tb[(uint64_t)(n0 + u) * tstride + it * 32] = 0;
+              }
+              mv = min8(mv, v[u]);
+              if (ADV) __stcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at, inc8(v[u]));
+            }
+          }
         }
         if (g) __stcs(g + at, mv);
         if (HOT) {
