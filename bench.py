@@ -27,6 +27,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import time
 
 import numpy as np
 
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--touch-chunk-mib", type=int, default=0, help="touch bits per chunk of the fused slot")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     return ap.parse_args()
 
 
@@ -174,9 +176,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, chunk: int):
     """DRAM bytes per chunk launch of the streaming pass from the committed ncu summary, if
-    the kernel source has not changed since it was captured."""
+    the kernel source has not changed since it was captured and the launch covers as many
+    estimators as the captured one."""
     path = os.path.join(ROOT, "profiles", f"chunk_pass_{workload}.md")
     try:
         text = open(path).read()
@@ -184,7 +187,8 @@ def profiled_traffic(workload: str):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    c = re.search(r"chunk_estimators:\s*([0-9]+)", text)
+    if not m or not h or not c or h.group(1) != kernel_source_hash() or int(c.group(1)) != chunk:
         return None
     return float(m.group(1))
 
@@ -279,10 +283,12 @@ def run_reference(args, world, rank):
 # -------------------------------------------------------------- our arm
 
 def batched_vs_plain(rank: int, local: int, name: str = "edge16_c3", fill: int = 4, warmup: int = 2,
-                     steps: int = 5) -> dict:
+                     steps: int = 5, tune: bool = True) -> dict:
     """The same slots of a many-router workload two ways, with identical lists required.
     plain: one ssd_scan per router, then ssd_merge, ssd_regain and ssd_advance;
-    batched: one ssd_scan_batch over all routers, then one ssd_close_slot."""
+    batched: one ssd_scan_batch over all routers, then one ssd_close_slot.
+    With tune, the autotuner picks the launch configuration once (on the first context's
+    fresh sketches) and both ways run under it."""
     import torch
 
     import paper_1803_11036_gb300 as ssd
@@ -300,10 +306,17 @@ def batched_vs_plain(rank: int, local: int, name: str = "edge16_c3", fill: int =
     stream = torch.cuda.Stream(dev)
     out = {}
     lists = {}
+    chosen, tune_s = None, 0.0
     for mode in ("plain", "batched"):
         ctx = ssd.Context(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]), device=local)
         routers = [ctx.sketch() for _ in range(R)]
         glob = ctx.sketch() if mode == "plain" else None
+        if tune and chosen is None:
+            t0 = time.perf_counter()
+            chosen = ctx.autotune(routers, slots[0], None, reps=2, stream=stream)
+            tune_s = time.perf_counter() - t0
+        if chosen is not None:
+            ctx.tuning = chosen
         got = []
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = 0
@@ -340,14 +353,17 @@ def batched_vs_plain(rank: int, local: int, name: str = "edge16_c3", fill: int =
             "batched": {**out["batched"], "mpps": round(timed / (out["batched"]["ms_per_slot"] * steps) / 1e3, 1)},
             "speedup": round(out["plain"]["ms_per_slot"] / out["batched"]["ms_per_slot"], 3),
             "identical_lists": bool(same), "window_filled_slots": fill,
+            "tuning": chosen, "tune_s": round(tune_s, 2),
             "note": "plain = per-router scans + merge + regain + advance; batched = one scan launch + fused close"}
 
 
 def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64, per_router: int = 4,
-               offered_per_s: float = 500.0) -> dict:
+               offered_per_s: float = 500.0, max_inflight: int = 16, tuning: dict | None = None) -> dict:
     """Routers stream slices at Poisson times; each slice is scanned and closed on its router's
-    resident RSEA as soon as the device has room (continuous batching, at most 16 in flight).
-    Latency runs from a slice's arrival to its list on the host."""
+    resident RSEA as soon as the device has room (continuous batching, at most max_inflight in
+    flight). Latency runs from a slice's arrival to its list on the host. Slices arrive in
+    pinned buffers that have crossed the host link once before the clock starts, as the
+    reused receive buffers of a deployment would have."""
     import torch
 
     import paper_1803_11036_gb300 as ssd
@@ -355,6 +371,7 @@ def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64
     from paper_1803_11036_gb300 import serve
 
     W = replica_workload(name, rank)
+    dev = torch.device("cuda", local)
     rng = np.random.default_rng(11 + rank)
     gap = routers / offered_per_s          # mean gap between one router's slices
     slices = []
@@ -368,8 +385,13 @@ def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64
             t += rng.exponential(gap)
             host = torch.from_numpy(v.reshape(-1).view(np.int32)).pin_memory()
             slices.append(serve.Slice(router=r, pairs=host, arrival=t, seq=j))
+    warm = torch.empty(max(s.pairs.numel() for s in slices), dtype=torch.int32, device=dev)
+    for s in slices:
+        warm[:s.pairs.numel()].copy_(s.pairs, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    del warm
     srv = serve.Server(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]), device=local,
-                       max_inflight=16)
+                       max_inflight=max_inflight, max_slice_pairs=int(W["traffic"]["count_b"]), tuning=tuning)
     for r in range(routers):               # admit every router before the clock starts
         if not srv.try_admit(r):
             break
@@ -378,8 +400,9 @@ def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64
     srv.close()
     out = serve.latency_summary(res)
     out.update({"workload": name, "routers": admitted, "q": W["params"]["q"],
-                "offered_slices_per_s": offered_per_s, "max_inflight": 16,
-                "slice_packets": "uniform [10k, 2M]"})
+                "offered_slices_per_s": offered_per_s, "max_inflight": max_inflight,
+                "slice_packets": "uniform [10k, 2M]", "reserved_slice_pairs": int(W["traffic"]["count_b"]),
+                "tuning": tuning or "default"})
     return out
 
 
@@ -413,6 +436,12 @@ def run_ours(args, world, rank, local):
                       tg.hash_tables(W["hash_seed"]), device=local)
     routers = [ctx.sketch() for _ in range(R)]
     stream = torch.cuda.Stream(dev)
+    default_tuning = ctx.tuning
+    tune_s = 0.0
+    if not args.no_tune:   # launch configuration picked by measurement on the first slot
+        t0 = time.perf_counter()
+        ctx.autotune(routers, slot_dev[0], None, reps=3, stream=stream)
+        tune_s = time.perf_counter() - t0
     cap = 1 << 16
     ips = torch.empty(cap, dtype=torch.int32, device=dev)
     rks = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -465,6 +494,25 @@ def run_ours(args, world, rank, local):
     all_pk = sum_over_ranks(timed_pk, world)
     value = all_pk / (max_ms / 1e3) / 1e6
 
+    # ---- the same slots under the default launch configuration, for the tuner's record
+    default_leg = None
+    tuned = ctx.tuning
+    if not args.no_tune:
+        n_def = min(args.steps, 10)
+        ctx.tuning = default_tuning
+        da, db = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            step(fill + args.warmup)         # warm-up
+            da.record(stream)
+            for i in range(n_def):
+                step(fill + args.warmup + i)
+            db.record(stream)
+        stream.synchronize()
+        ctx.tuning = tuned
+        def_ms = da.elapsed_time(db) / n_def
+        default_leg = {"ms_per_slot": round(def_ms, 4), "tuned_ms_per_slot": round(total_ms / args.steps, 4),
+                       "slots": n_def, "configuration": default_tuning}
+
     # ---- the scan alone (Algorithm 2 writing the recorders directly), on the timed slices
     scratch = [ctx.sketch() for _ in range(R)]
     sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -508,14 +556,14 @@ def run_ours(args, world, rank, local):
     pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
     avg_pass_s = statistics.mean(pass_ms) / 1e3
     achieved = pass_bytes / avg_pass_s / 1e9
-    # the pass runs as chunk launches of `chunk` estimators (touch bits of 32 MiB per chunk)
+    # the pass runs as chunk launches of `chunk` estimators (the tuned touch bits per chunk)
     n_se = r * C
     chunk = 1
-    while chunk * 2 * (eta // 8) * R <= (args.touch_chunk_mib << 20 or 32 << 20) and chunk * 2 <= 1 << (n_se - 1).bit_length():
+    while chunk * 2 * (eta // 8) * R <= tuned["touch_chunk_bytes"] and chunk * 2 <= 1 << (n_se - 1).bit_length():
         chunk *= 2
     n_chunks = -(-n_se // chunk)
     peak, peak_kind = measured_peak()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, chunk)
     scan_alg_bytes = 8 + 2 * r                  # pair read + r recorder writes per packet
 
     # ---- end to end through the C ABI from pinned host memory: ssd_slot_host copies each
@@ -531,7 +579,17 @@ def run_ours(args, world, rank, local):
                  torch.zeros(1, dtype=torch.int64, device=dev)) for _ in range(2)]
         hbuf = [(torch.empty(head, dtype=torch.int32).pin_memory(), torch.empty(head, dtype=torch.int32).pin_memory(),
                  torch.zeros(1, dtype=torch.int64).pin_memory()) for _ in range(2)]
-        done = [torch.cuda.Event() for _ in range(len(host))]
+        # every pinned buffer crosses the host link once before the clock starts: a DMA through
+        # freshly pinned pages can run an order of magnitude slower than through pages already
+        # mapped, and a deployment reuses its pinned buffers
+        warm = [torch.empty(x.numel(), dtype=x.dtype, device=dev) for x in host[0]]
+        with torch.cuda.stream(stream):
+            for hs in host:
+                for dst, src in zip(warm, hs):
+                    dst.copy_(src, non_blocking=True)
+        stream.synchronize()
+        del warm
+        done = [torch.cuda.Event(enable_timing=True) for _ in range(len(host))]
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         d2h = 0
         with torch.cuda.stream(stream):
@@ -556,24 +614,30 @@ def run_ours(args, world, rank, local):
                         d2h += 8 + 2 * 4 * head
             eb.record(stream)
         stream.synchronize()
-        # the host link alone: one slot's pairs, pinned host -> device, 5 times
+        # device time between consecutive slot completions (the slot's own pace on the GPU)
+        gaps = [done[j - 1].elapsed_time(done[j]) for j in range(2, len(host))]
+        # the host link alone: every timed slot's pinned pairs, host -> device, once each
         probe = [torch.empty(x.numel(), dtype=x.dtype, device=dev) for x in host[0]]
-        ha, hb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per = []
         with torch.cuda.stream(stream):
-            ha.record(stream)
-            for _ in range(5):
-                for dst, src in zip(probe, host[0]):
+            for hs in host[1:]:
+                ha, hb_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ha.record(stream)
+                for dst, src in zip(probe, hs):
                     dst.copy_(src, non_blocking=True)
-            hb_.record(stream)
+                hb_.record(stream)
+                per.append((ha, hb_, sum(x.numel() * 4 for x in hs)))
         stream.synchronize()
-        h2d_gbs = 5 * sum(x.numel() * 4 for x in host[0]) / (ha.elapsed_time(hb_) / 1e3) / 1e9
+        rates = [b / (a.elapsed_time(c) / 1e3) / 1e9 for a, c, b in per]
+        h2d_gbs = statistics.median(rates)
         del probe
         e2e_ms = max_over_ranks(ea.elapsed_time(eb), world)
         e2e = {"value": round(all_pk / (e2e_ms / 1e3) / 1e6, 2), "unit": "Mpps",
                "h2d_bytes_per_step": int(8 * timed_pk / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps),
                "path": "ssd_slot_host from pinned buffers, list read back every slot",
-               "host_to_device_gbs": round(h2d_gbs, 1)}
+               "host_to_device_gbs": round(h2d_gbs, 1), "host_to_device_gbs_min": round(min(rates), 1),
+               "slot_completion_ms": {"median": round(statistics.median(gaps), 4), "max": round(max(gaps), 4)}}
         del host
 
     del slot_dev, routers
@@ -592,7 +656,10 @@ def run_ours(args, world, rank, local):
         "config": {"workload": args.workload, "routers": R, "packets_per_slot": int(pk_per_slot[-1]),
                    "k": k, "eta": eta, "q": prm["q"], "r": r, "delta": prm["delta"], "theta": prm["theta"],
                    "window_filled_slots": fill, "l2": "inputs larger than L2: the 5 GiB RSEA is streamed every "
-                   "step and each step scans a distinct slice"},
+                   "step and each step scans a distinct slice",
+                   "tuning": tuned, "tuned_by": "default" if args.no_tune else "ssd_autotune on the first slot",
+                   "tune_s": round(tune_s, 2)},
+        "default_configuration": default_leg,
         "gbps_at_800B": gbps(value),
         "scan": {"mpps": round(scan_mpps, 2), "gbps_at_800B": gbps(scan_mpps), "ms_per_slice": round(scan_ms, 4),
                  "achieved_gbs_algorithmic": round(scan_alg_bytes * timed_pk / (scan_ms * args.steps / 1e3) / 1e9, 1),

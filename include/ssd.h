@@ -278,6 +278,56 @@ SSD_API int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32
  * (stream capture cannot allocate). Waits for the device. */
 SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
 
+/* Launch configuration of a context's kernels. The paper has no counterpart:
+ * these choices set only how the work of Algorithms 2 and 5 and of the
+ * streaming pass (Sec. 4.3) is spread over the GPU. No value changes a
+ * recorder, a list or a counter. Defaults: touch_chunk_bytes of the params, 0, 8,
+ * 4, 8, 0.
+ *   touch_chunk_bytes: touch bits of one chunk of ssd_slot (64 KiB .. 1 GiB,
+ *       rounded up to 256 B; chunk sizes are powers of two that fit it);
+ *   stream_blocks_per_sm: resident blocks per SM of the streaming and chunk
+ *       kernels (0 = as many as fit, else at most this many, 1..8);
+ *   scan_blocks_per_sm: the scan, touch and pre-hash kernels launch at most
+ *       SMs x this many blocks (1..32);
+ *   scan_unroll: 16-byte pair vectors one thread loads before hashing them
+ *       (items per thread per step: 1, 2, 4 or 8);
+ *   merge_group: routers whose recorders one lane loads before it stores any
+ *       of them in the multi-router streaming pass (the merge tile: 2, 4 or 8);
+ *   combine_touches: 1 = the lanes of a warp whose touch bits fall into one
+ *       32-bit word OR them together (__match_any_sync) and issue one atomic,
+ *       which helps when a few sources send much of the traffic; 0 = one
+ *       atomic per touch. */
+typedef struct ssd_tuning {
+  uint64_t touch_chunk_bytes;
+  uint32_t stream_blocks_per_sm;
+  uint32_t scan_blocks_per_sm;
+  uint32_t scan_unroll;
+  uint32_t merge_group;
+  uint32_t combine_touches;
+  uint32_t reserved; /* must be 0 */
+} ssd_tuning;
+
+/* The context's current launch configuration (host only). */
+SSD_API int ssd_tuning_get(const ssd_ctx* ctx, ssd_tuning* out);
+/* Replace the launch configuration. SSD_EINVAL (nothing changed) for a value
+ * outside the ranges above. A new touch_chunk_bytes reallocates the two touch
+ * buffers after waiting for the device (make the call before any stream
+ * capture; SSD_ENOMEM leaves the old configuration). */
+SSD_API int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t);
+/* Pick the launch configuration by measurement: run ssd_slot on the n routers
+ * (and `global` when not NULL) with the given pairs - one representative slot,
+ * device memory, as in ssd_slot - once per candidate value of one field at a
+ * time, the others held at the best so far (two sweeps over the fields), `reps`
+ * timed slots per candidate (1..16, the median counts) after one untimed one.
+ * The fastest configuration is set on the context and written to *out (when
+ * not NULL). The routers and `global` must not have run a slot yet (slot 0,
+ * else SSD_ESTATE) and are returned to their initial state afterwards: every
+ * recorder 65535, slot 0 (recorders scanned before the call are lost). Waits
+ * for the device; not for use inside a stream capture. */
+SSD_API int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs,
+                         const uint64_t* n_pairs, int n, ssd_sketch* global, int reps, ssd_tuning* out,
+                         void* stream);
+
 /* Counters of the context's last regain or close (waits for `stream`). */
 SSD_API int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream);
 

@@ -25,7 +25,7 @@ import numpy as np
 from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SLOT_CHUNKED,  # noqa: F401
                    SSD_STATUS_CTB_OVERFLOW,
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
-                   Params, SSDError, Stats, check, load)
+                   TUNING_FIELDS, Params, SSDError, Stats, Tuning, check, load)
 
 __all__ = ["Context", "Sketch", "SlotGraph", "SSDError", "SSD_VERIFY_H0", "SSD_NO_PRUNE", "make_params",
            "threshold", "params_ok", "library_path"]
@@ -327,6 +327,43 @@ class Context:
     def reserve(self, max_pairs: int) -> None:
         """Allocate what slot()/slot_host() allocate on a first call with up to max_pairs pairs."""
         check(self.L.ssd_reserve(self._h, max_pairs), "ssd_reserve")
+
+    @property
+    def tuning(self) -> dict:
+        """The launch configuration (ssd_tuning fields); no field changes a result."""
+        t = Tuning()
+        check(self.L.ssd_tuning_get(self._h, ctypes.byref(t)), "ssd_tuning_get")
+        return {f: int(getattr(t, f)) for f in TUNING_FIELDS}
+
+    @tuning.setter
+    def tuning(self, value: dict) -> None:
+        cur = self.tuning
+        unknown = set(value) - set(TUNING_FIELDS)
+        if unknown:
+            raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+        cur.update({k: int(v) for k, v in value.items()})
+        t = Tuning(**cur)
+        check(self.L.ssd_tuning_set(self._h, ctypes.byref(t)), "ssd_tuning_set")
+
+    def autotune(self, routers, pairs_list, global_sketch: Sketch | None = None, reps: int = 3,
+                 stream=None) -> dict:
+        """Pick the launch configuration by timing ssd_slot on one representative slot of pairs
+        (device tensors, one per router). The sketches must not have run a slot yet and come back
+        in their initial state. Returns the chosen configuration, which the context keeps."""
+        if len(routers) != len(pairs_list):
+            raise ValueError("one pair tensor per router")
+        ptrs, counts = [], []
+        for t in pairs_list:
+            p, n = _pairs_ptr(t, self.device)
+            ptrs.append(p.value or 0)
+            counts.append(n)
+        P = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        N = (ctypes.c_uint64 * len(counts))(*counts)
+        out = Tuning()
+        check(self.L.ssd_autotune(self._h, _handles(routers), P, N, len(routers),
+                                  global_sketch._h if global_sketch is not None else None, reps,
+                                  ctypes.byref(out), _stream_handle(stream, self.device)), "ssd_autotune")
+        return {f: int(getattr(out, f)) for f in TUNING_FIELDS}
 
     def stats(self, stream=None) -> dict:
         st = Stats()

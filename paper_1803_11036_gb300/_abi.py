@@ -34,6 +34,17 @@ class Stats(ctypes.Structure):
                 ("raw", ctypes.c_uint64), ("n_out", ctypes.c_uint64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("touch_chunk_bytes", ctypes.c_uint64), ("stream_blocks_per_sm", ctypes.c_uint32),
+                ("scan_blocks_per_sm", ctypes.c_uint32), ("scan_unroll", ctypes.c_uint32),
+                ("merge_group", ctypes.c_uint32), ("combine_touches", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+TUNING_FIELDS = ("touch_chunk_bytes", "stream_blocks_per_sm", "scan_blocks_per_sm", "scan_unroll", "merge_group",
+                 "combine_touches")
+
+
 # name -> (argtypes, restype); the exported ABI, in header order
 _vp, _u32, _u64, _int = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 _PP = ctypes.POINTER(Params)
@@ -60,6 +71,9 @@ SIGNATURES = {
     "ssd_slot": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_slot_host": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_reserve": ([_vp, _u64], _int),
+    "ssd_tuning_get": ([_vp, ctypes.POINTER(Tuning)], _int),
+    "ssd_tuning_set": ([_vp, ctypes.POINTER(Tuning)], _int),
+    "ssd_autotune": ([_vp, _vp, _vp, _vp, _int, _vp, _int, ctypes.POINTER(Tuning), _vp], _int),
     "ssd_set_trace": ([_vp, _vp, _vp, _vp], _int),
     "ssd_stats_get": ([_vp, ctypes.POINTER(Stats), _vp], _int),
     "ssd_launch_count": ([_vp], _u64),

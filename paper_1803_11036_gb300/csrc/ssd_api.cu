@@ -33,6 +33,7 @@ struct ssd_ctx {
   // fused slot: double-buffered touch bits and the side stream that fills them
   uint32_t* touch[2];
   uint64_t touch_bytes;
+  ssd::Tuning tn;             // launch configuration (ssd_tuning_set / ssd_autotune)
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_touched[2], ev_closed[2];
   // pre-hashed pairs of the one-router fused slot (grown to the largest slot)
@@ -127,13 +128,19 @@ int add_job(ssd::ScanBatch& b, int j, uint16_t* dr, const uint32_t* pairs, uint6
   return SSD_OK;
 }
 
+// Blocks of a scan, touch or pre-hash launch over nvec pair vectors: enough for
+// one step of scan_unroll vectors per thread, at most SMs x scan_blocks_per_sm.
+uint64_t scan_grid(const ssd_ctx* ctx, uint64_t nvec) {
+  const uint64_t per = (uint64_t)ssd::kBlock * ctx->tn.unroll;
+  uint64_t grid = (nvec + per - 1) / per;
+  const uint64_t cap = (uint64_t)ctx->sms * ctx->tn.scan_bps;
+  if (grid > cap) grid = cap;
+  return grid < 1 ? 1 : grid;
+}
+
 int scan_jobs(ssd_ctx* ctx, ssd::ScanBatch& b, uint64_t total_vec, bool any_edge, cudaStream_t st) {
   if (total_vec == 0 && !any_edge) return SSD_OK;
-  uint64_t grid = (total_vec + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
-  const uint64_t cap = (uint64_t)ctx->sms * 8;
-  if (grid > cap) grid = cap;
-  if (grid < 1) grid = 1;
-  cudaError_t e = ssd::launch_scan(ctx->d, ctx->tables, b, (int)grid, st);
+  cudaError_t e = ssd::launch_scan(ctx->d, ctx->tables, b, (int)scan_grid(ctx, total_vec), ctx->tn, st);
   if (e != cudaSuccess) return cuda_fail(e, "scan kernel");
   ctx->launches += 1;
   return SSD_OK;
@@ -145,7 +152,7 @@ int stream_pass(ssd_ctx* ctx, ssd_sketch* const* routers, int n, uint16_t* globa
   a.n = n;
   for (int i = 0; i < n; ++i) a.routers[i] = routers[i]->dr;
   a.global = global;
-  cudaError_t e = ssd::launch_stream(ctx->d, ctx->s, a, mode, ctx->sms, st);
+  cudaError_t e = ssd::launch_stream(ctx->d, ctx->s, a, mode, ctx->sms, ctx->tn, st);
   if (e != cudaSuccess) return cuda_fail(e, "stream kernel");
   ctx->launches += 1;
   return SSD_OK;
@@ -208,7 +215,7 @@ void free_ctx(ssd_ctx* c) {
 
 extern "C" {
 
-int ssd_version(void) { return 100; }
+int ssd_version(void) { return 101; }
 
 const char* ssd_strerror(int code) {
   switch (code) {
@@ -257,6 +264,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   std::memset(c, 0, sizeof(*c));
   c->p = *p;
   c->device = device;
+  c->tn = ssd::default_tuning();
   cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "cudaDeviceGetAttribute"); }
 
@@ -561,9 +569,7 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   int rc = add_job(b, 0, router->dr, pairs, n_pairs, &nvec);
   if (rc != SSD_OK) return rc;
   b.prefix[1] = nvec;
-  uint64_t tgrid = (nvec + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
-  if (tgrid > (uint64_t)ctx->sms * 8) tgrid = (uint64_t)ctx->sms * 8;
-  if (tgrid < 1) tgrid = 1;
+  const uint64_t tgrid = scan_grid(ctx, nvec);
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
   // both hashes of every pair once per slot when they pack into one word
@@ -601,13 +607,13 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
     a.edge[0] = (n_pairs & 1) ? reinterpret_cast<const uint32_t*>(ctx->packed + (n_pairs - 1)) : nullptr;
     a.edge[1] = nullptr;
     e = ssd::launch_touch_packed(d, a.vec, a.nvec, reinterpret_cast<const uint2*>(a.edge[0]), ctx->touch[0], 0,
-                                 cnt0, (int)tgrid, st);
+                                 cnt0, (int)tgrid, ctx->tn, st);
   } else {
     a.vec = b.vec[0];
     a.nvec = nvec;
     a.edge[0] = b.edge[0];
     a.edge[1] = b.edge[1];
-    e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[0], 0, cnt0, (int)tgrid, st);
+    e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[0], 0, cnt0, (int)tgrid, ctx->tn, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
   ctx->launches += 1;
@@ -623,7 +629,7 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
       a.next = nullptr;
       a.nx_se0 = a.nx_count = 0;
     }
-    e = ssd::launch_chunk(d, ctx->s, a, ctx->sms, st);
+    e = ssd::launch_chunk(d, ctx->s, a, ctx->sms, ctx->tn, st);
     if (e != cudaSuccess) return cuda_fail(e, "chunk kernel");
     ctx->launches += 1;
   }
@@ -674,9 +680,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
     if (rc != SSD_OK) return rc;
   }
   b.prefix[n] = prefix;
-  uint64_t tgrid = (prefix + (uint64_t)ssd::kBlock * 4 - 1) / ((uint64_t)ssd::kBlock * 4);
-  if (tgrid > (uint64_t)ctx->sms * 8) tgrid = (uint64_t)ctx->sms * 8;
-  if (tgrid < 1) tgrid = 1;
+  const uint64_t tgrid = scan_grid(ctx, prefix);
 
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
@@ -695,7 +699,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
     const uint64_t se0 = c * count;
     const uint64_t cnt = n_se - se0 < count ? n_se - se0 : count;
     if (c >= 2) SSD_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_closed[bsel], 0));  // buffer cleared
-    cudaError_t e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[bsel], se0, cnt, (int)tgrid, ctx->side);
+    cudaError_t e = ssd::launch_touch(d, ctx->tables, b, ctx->touch[bsel], se0, cnt, (int)tgrid, ctx->tn, ctx->side);
     if (e != cudaSuccess) return cuda_fail(e, "touch kernel");
     ctx->launches += 1;
     SSD_CUDA(cudaEventRecord(ctx->ev_touched[bsel], ctx->side));
@@ -703,7 +707,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
     a.se0 = se0;
     a.se_count = cnt;
     a.touch = reinterpret_cast<uint8_t*>(ctx->touch[bsel]);
-    e = ssd::launch_stream(d, ctx->s, a, ssd::kAdvance | ssd::kHot, ctx->sms, st);
+    e = ssd::launch_stream(d, ctx->s, a, ssd::kAdvance | ssd::kHot, ctx->sms, ctx->tn, st);
     if (e != cudaSuccess) return cuda_fail(e, "stream kernel");
     ctx->launches += 1;
     SSD_CUDA(cudaEventRecord(ctx->ev_closed[bsel], st));
@@ -823,5 +827,172 @@ int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
 }
 
 uint64_t ssd_launch_count(const ssd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int ssd_tuning_get(const ssd_ctx* ctx, ssd_tuning* out) {
+  if (!ctx || !out) return SSD_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->touch_chunk_bytes = ctx->touch_bytes;
+  out->stream_blocks_per_sm = ctx->tn.stream_bps;
+  out->scan_blocks_per_sm = ctx->tn.scan_bps;
+  out->scan_unroll = ctx->tn.unroll;
+  out->merge_group = ctx->tn.group;
+  out->combine_touches = ctx->tn.combine;
+  return SSD_OK;
+}
+
+int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
+  if (!ctx || !t || t->reserved) return SSD_EINVAL;
+  if (t->touch_chunk_bytes < (64ull << 10) || t->touch_chunk_bytes > (1ull << 30)) return SSD_EINVAL;
+  if (t->stream_blocks_per_sm > 8 || t->scan_blocks_per_sm < 1 || t->scan_blocks_per_sm > 32) return SSD_EINVAL;
+  const uint32_t u = t->scan_unroll, g = t->merge_group;
+  if (u != 1 && u != 2 && u != 4 && u != 8) return SSD_EINVAL;
+  if (g != 2 && g != 4 && g != 8) return SSD_EINVAL;
+  if (t->combine_touches > 1) return SSD_EINVAL;
+  const uint64_t bytes = (t->touch_chunk_bytes + 255) & ~255ull;
+  if (bytes != ctx->touch_bytes) {  // new touch buffers, zeroed, before the old ones go
+    DeviceGuard dg(ctx->device);
+    SSD_CUDA(cudaDeviceSynchronize());
+    uint32_t* nb[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&nb[i], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(nb[0]);
+        return SSD_ENOMEM;
+      }
+    }
+    cudaError_t e = cudaMemset(nb[0], 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(nb[1], 0, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      cudaFree(nb[0]);
+      cudaFree(nb[1]);
+      return cuda_fail(e, "ssd_tuning_set");
+    }
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(ctx->touch[i]);
+      ctx->touch[i] = nb[i];
+    }
+    ctx->touch_bytes = bytes;
+  }
+  ctx->tn.stream_bps = t->stream_blocks_per_sm;
+  ctx->tn.scan_bps = t->scan_blocks_per_sm;
+  ctx->tn.unroll = u;
+  ctx->tn.group = g;
+  ctx->tn.combine = t->combine_touches;
+  return SSD_OK;
+}
+
+int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs,
+                 const uint64_t* n_pairs, int n, ssd_sketch* global, int reps, ssd_tuning* out, void* stream) {
+  ssd_ctx* c2 = nullptr;
+  if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx || !d_pairs || !n_pairs) return SSD_EINVAL;
+  if (reps < 1 || reps > 16) return SSD_EINVAL;
+  if (global && global->ctx != ctx) return SSD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (routers[i] == global) return SSD_EINVAL;
+    if (routers[i]->slot != 0) return SSD_ESTATE;
+  }
+  if (global && global->slot != 0) return SSD_ESTATE;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  for (int i = 0; i < 2; ++i) SSD_CUDA(cudaEventCreate(&ev[i]));
+  ssd_tuning start;
+  ssd_tuning_get(ctx, &start);
+
+  // median time of `reps` slots under t, after one untimed slot (which also
+  // makes any first-call allocation of ssd_slot)
+  auto measure = [&](const ssd_tuning& t, float* ms) -> int {
+    int rc = ssd_tuning_set(ctx, &t);
+    if (rc != SSD_OK) return rc;
+    float v[16];
+    for (int i = -1; i < reps; ++i) {
+      if (i >= 0 && cudaEventRecord(ev[0], st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune");
+      rc = ssd_slot(ctx, routers, d_pairs, n_pairs, n, global, nullptr, nullptr, 0, nullptr, stream);
+      if (rc != SSD_OK) return rc;
+      if (i < 0) continue;
+      cudaError_t e = cudaEventRecord(ev[1], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&v[i], ev[0], ev[1]);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    }
+    for (int i = 1; i < reps; ++i)  // insertion sort of at most 16 values
+      for (int j = i; j > 0 && v[j] < v[j - 1]; --j) {
+        const float x = v[j]; v[j] = v[j - 1]; v[j - 1] = x;
+      }
+    *ms = v[reps / 2];
+    return SSD_OK;
+  };
+
+  // coordinate descent: one field at a time over its candidates, two sweeps; a
+  // new value must beat the current one (measured again beside it) by 1 %
+  ssd_tuning best = start;
+  int rc = SSD_OK;
+  for (int sweep = 0; sweep < 2 && rc == SSD_OK; ++sweep) {
+    for (int field = 0; field < 6 && rc == SSD_OK; ++field) {
+      uint64_t cand[8];
+      int nc = 0;
+      switch (field) {
+        case 0: for (uint64_t m : {8ull, 16ull, 32ull, 64ull}) cand[nc++] = m << 20; break;
+        case 1: for (uint64_t b : {0ull, 1ull, 2ull, 3ull}) cand[nc++] = b; break;
+        case 2: for (uint64_t b : {2ull, 4ull, 8ull, 16ull, 32ull}) cand[nc++] = b; break;
+        case 3: for (uint64_t u : {1ull, 2ull, 4ull, 8ull}) cand[nc++] = u; break;
+        case 4: if (n > 1) for (uint64_t g : {2ull, 4ull, 8ull}) cand[nc++] = g; break;
+        default: for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
+      }
+      auto with = [&](uint64_t v) {
+        ssd_tuning t = best;
+        switch (field) {
+          case 0: t.touch_chunk_bytes = v; break;
+          case 1: t.stream_blocks_per_sm = (uint32_t)v; break;
+          case 2: t.scan_blocks_per_sm = (uint32_t)v; break;
+          case 3: t.scan_unroll = (uint32_t)v; break;
+          case 4: t.merge_group = (uint32_t)v; break;
+          default: t.combine_touches = (uint32_t)v; break;
+        }
+        return t;
+      };
+      if (nc == 0) continue;
+      float cur = 0.f;
+      rc = measure(best, &cur);
+      ssd_tuning pick = best;
+      float pick_ms = cur;
+      for (int i = 0; i < nc && rc == SSD_OK; ++i) {
+        const ssd_tuning t = with(cand[i]);
+        if (std::memcmp(&t, &best, sizeof(t)) == 0) continue;
+        float ms = 0.f;
+        rc = measure(t, &ms);
+        if (rc == SSD_ENOMEM && field == 0) {  // touch buffers of that size do not fit: skip it
+          rc = SSD_OK;
+          continue;
+        }
+        if (rc == SSD_OK && ms < pick_ms && ms < 0.99f * cur) {
+          pick = t;
+          pick_ms = ms;
+        }
+      }
+      best = pick;
+    }
+  }
+  // the chosen configuration (the starting one when something failed), and the
+  // sketches back in their initial state
+  int rc2 = ssd_tuning_set(ctx, rc == SSD_OK ? &best : &start);
+  if (rc == SSD_OK) rc = rc2;
+  cudaError_t e = cudaSuccess;
+  const uint64_t bytes = ssd_sketch_bytes(ctx);
+  for (int i = 0; i < n + 1 && e == cudaSuccess; ++i) {
+    ssd_sketch* sk = i < n ? routers[i] : global;
+    if (!sk) continue;
+    e = cudaMemsetAsync(sk->dr, 0xFF, bytes, st);
+    sk->slot = 0;
+  }
+  // the tuning slots ran with no list capacity: clear the status they left
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (int i = 0; i < 2; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess && rc == SSD_OK) rc = cuda_fail(e, "autotune reset");
+  if (rc == SSD_OK && out) ssd_tuning_get(ctx, out);
+  return rc;
+}
 
 }  // extern "C"

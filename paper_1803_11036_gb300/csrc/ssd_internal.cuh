@@ -46,6 +46,17 @@ struct Scratch {
   DevCounters* counters;
 };
 
+// Launch configuration (ssd_tuning without the touch buffer size). No field
+// changes a result; each one only spreads the same work differently.
+struct Tuning {
+  uint32_t stream_bps;   // resident blocks per SM of the streaming kernels (0 = all that fit)
+  uint32_t scan_bps;     // scan / touch / pre-hash grid = SMs x scan_bps at most
+  uint32_t unroll;       // pair vectors per thread per step: 1, 2, 4, 8
+  uint32_t group;        // routers loaded per lane before storing, multi-router pass: 2, 4, 8
+  uint32_t combine;      // combine same-word touch atomics inside a warp
+};
+inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u}; }
+
 // ---- scan (ssd_scan.cu) ----
 constexpr int kMaxBatch = SSD_MAX_ROUTERS;
 struct ScanJob {
@@ -62,7 +73,8 @@ struct ScanBatch {
   const uint4* vec[kMaxBatch];
   const uint32_t* edge[2 * kMaxBatch];  // head, tail per router (nullptr when absent)
 };
-cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, cudaStream_t st);
+cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, const Tuning& tn,
+                        cudaStream_t st);
 
 // ---- streaming passes (ssd_stream.cu) ----
 struct StreamArgs {
@@ -78,15 +90,14 @@ struct StreamArgs {
 // mode bits
 constexpr int kAdvance = 1;   // routers += 1 (saturating) after reading
 constexpr int kHot = 2;       // count R_k of the merged value and pool the hot estimators
-// spare_blocks: resident blocks per SM left free for a concurrent kernel (0 = none)
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
-                          cudaStream_t st, int spare_blocks = 0);
+                          const Tuning& tn, cudaStream_t st);
 
 // ---- touch collection for the fused slot (ssd_scan.cu) ----
 // Algorithm 2 for the estimators [se0, se0 + se_count) only: instead of storing
 // 0 into the recorder, set its bit in `bits` (layout of StreamArgs::touch).
 cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
-                         uint64_t se_count, int grid, cudaStream_t st);
+                         uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st);
 
 // ---- device helpers shared by the scan and streaming kernels ----
 // Simple tabulation: four 256-word tables indexed by the bytes of x, XORed.
@@ -94,11 +105,31 @@ __device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
   return T[x & 255u] ^ T[256u + ((x >> 8) & 255u)] ^ T[512u + ((x >> 16) & 255u)] ^ T[768u + (x >> 24)];
 }
 
+// Sets bit `bit` of `bits` (an L2-resident touch buffer) when ok. With COMBINE
+// all 32 lanes of the warp must make the call together: lanes whose bits fall
+// into one 32-bit word are grouped (__match_any_sync on the word index), the
+// group ORs its bits (__reduce_or_sync over the group's mask) and its lowest
+// lane issues the one atomic. Lanes with ok == false join with a key no word has.
+template <bool COMBINE>
+__device__ __forceinline__ void set_touch(uint32_t* bits, uint64_t bit, bool ok) {
+  if (COMBINE) {
+    const unsigned long long word = ok ? (unsigned long long)(bit >> 5) : ~0ull;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, word);
+    const unsigned v = __reduce_or_sync(grp, ok ? (1u << (bit & 31u)) : 0u);
+    if (ok && (threadIdx.x & 31u) == (unsigned)(__ffs(grp) - 1)) atomicOr(bits + word, v);
+  } else if (ok) {
+    atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
+  }
+}
+
 // Algorithm 2 for the estimators [se0, se0 + count) only (one chunk, inside one
 // row or whole rows): the recorder a pair sets to 0 is marked in `bits` instead
 // (router base jbase = router * count; estimator se0 + e, recorder x -> bit
-// (jbase + e) * eta + x). sT holds both table sets (2048 words).
-__device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint32_t cip, uint32_t oip,
+// (jbase + e) * eta + x). sT holds both table sets (2048 words). `live` = false
+// makes the call a no-op (a lane past the end of the pairs; with COMBINE every
+// lane calls).
+template <bool COMBINE>
+__device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint32_t cip, uint32_t oip, bool live,
                                            const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
                                            uint64_t se0, uint64_t count) {
   const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
@@ -110,16 +141,15 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    if (e < count) {
-      if (x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
-      const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
-      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
-    }
+    const bool ok = live && e < count;
+    if (ok && x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
+    set_touch<COMBINE>(bits, ((jbase + e) << d.log2_eta) | x, ok);
   }
 }
 
 // touch_pair on a pre-hashed pair: packed = RHFG[0](cip) | H1(oip) << q (q + log2_eta <= 32).
-__device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint32_t packed, const Dims& d,
+template <bool COMBINE>
+__device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint32_t packed, bool live, const Dims& d,
                                              uint32_t r0, uint32_t r1, uint64_t se0, uint64_t count) {
   const uint32_t c0 = packed & d.col_mask;
   const uint32_t x = packed >> d.q;
@@ -130,10 +160,7 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    if (e < count) {
-      const uint64_t bit = (e << d.log2_eta) | x;
-      atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
-    }
+    set_touch<COMBINE>(bits, (e << d.log2_eta) | x, live && e < count);
   }
 }
 
@@ -146,7 +173,7 @@ cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatc
 // Algorithm 2 for one chunk from pre-hashed pairs (one router): `vec` holds nvec
 // vectors of two packed pairs, `tail` one more packed pair or nullptr.
 cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
-                                uint64_t se0, uint64_t se_count, int grid, cudaStream_t st);
+                                uint64_t se0, uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st);
 
 // ---- one chunk of the fused slot of one router (ssd_stream.cu) ----
 // The streaming pass over estimators [se0, se0 + count) with that chunk's touch
@@ -164,7 +191,8 @@ struct ChunkArgs {
   const uint32_t* edge[2];   // head / tail pair outside the body, or nullptr
   int packed;                // vec/edge[0] hold pre-hashed pairs (edge[1] unused)
 };
-cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
+                         cudaStream_t st);
 
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.

@@ -37,8 +37,8 @@ __device__ __forceinline__ int find_router(const ScanBatch& b, uint64_t v) {
   return lo;
 }
 
-constexpr int kUnroll = 4;
-
+// U: 16-byte pair vectors each thread loads before it hashes any of them.
+template <int U>
 __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* __restrict__ tables,
                                                  const __grid_constant__ ScanBatch b) {
   __shared__ uint32_t sT[2048];
@@ -58,12 +58,12 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
   if (b.n == 1) {
     const uint4* __restrict__ vec = b.vec[0];
     uint16_t* __restrict__ dr = b.dr[0];
-    for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
-      uint4 w[kUnroll];
+    for (; v + (U - 1) * stride < total; v += U * stride) {
+      uint4 w[U];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) w[u] = __ldcs(vec + v + u * stride);
+      for (int u = 0; u < U; ++u) w[u] = __ldcs(vec + v + u * stride);
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         scan_pair(dr, w[u].x, w[u].y, sT, d);
         scan_pair(dr, w[u].z, w[u].w, sT, d);
       }
@@ -74,18 +74,18 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
       scan_pair(dr, w.z, w.w, sT, d);
     }
   } else {
-    for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
-      uint4 w[kUnroll];
-      uint16_t* dr[kUnroll];
+    for (; v + (U - 1) * stride < total; v += U * stride) {
+      uint4 w[U];
+      uint16_t* dr[U];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         const uint64_t vv = v + u * stride;
         const int j = find_router(b, vv);
         w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
         dr[u] = b.dr[j];
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         scan_pair(dr[u], w[u].x, w[u].y, sT, d);
         scan_pair(dr[u], w[u].z, w[u].w, sT, d);
       }
@@ -99,6 +99,11 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
   }
 }
 
+// The touch kernels walk the vectors warp by warp (vb = the warp's first
+// vector, a multiple of 32 because the grid stride is): every lane of a warp
+// runs the same iterations, as set_touch<true> needs; a lane past the end only
+// takes part.
+template <int U, bool COMBINE>
 __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* __restrict__ tables,
                                                   const __grid_constant__ ScanBatch b, uint32_t* __restrict__ bits,
                                                   uint64_t se0, uint64_t count) {
@@ -106,34 +111,42 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
   __syncthreads();
   const uint32_t r0 = (uint32_t)(se0 >> d.q), r1 = (uint32_t)((se0 + count - 1) >> d.q);
+  const uint32_t lane = threadIdx.x & 31u;
   if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
     const uint32_t* e = b.edge[threadIdx.x];
-    if (e) touch_pair(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], sT, d, r0, r1, se0, count);
+    if (e) touch_pair<false>(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], true, sT, d, r0, r1, se0, count);
   }
   const uint64_t total = b.prefix[b.n];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; v + (kUnroll - 1) * stride < total; v += kUnroll * stride) {
-    uint4 w[kUnroll];
-    uint64_t jb[kUnroll];
+  uint64_t vb = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  for (; vb + 31 + (U - 1) * stride < total; vb += U * stride) {
+    uint4 w[U];
+    uint64_t jb[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t vv = v + u * stride;
+    for (int u = 0; u < U; ++u) {
+      const uint64_t vv = vb + lane + u * stride;
       const int j = b.n == 1 ? 0 : find_router(b, vv);
       w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
       jb[u] = (uint64_t)j * count;
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      touch_pair(bits, jb[u], w[u].x, w[u].y, sT, d, r0, r1, se0, count);
-      touch_pair(bits, jb[u], w[u].z, w[u].w, sT, d, r0, r1, se0, count);
+    for (int u = 0; u < U; ++u) {
+      touch_pair<COMBINE>(bits, jb[u], w[u].x, w[u].y, true, sT, d, r0, r1, se0, count);
+      touch_pair<COMBINE>(bits, jb[u], w[u].z, w[u].w, true, sT, d, r0, r1, se0, count);
     }
   }
-  for (; v < total; v += stride) {
-    const int j = b.n == 1 ? 0 : find_router(b, v);
-    const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
-    touch_pair(bits, (uint64_t)j * count, w.x, w.y, sT, d, r0, r1, se0, count);
-    touch_pair(bits, (uint64_t)j * count, w.z, w.w, sT, d, r0, r1, se0, count);
+  for (; vb < total; vb += stride) {
+    const uint64_t v = vb + lane;
+    const bool live = v < total;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    uint64_t jb = 0;
+    if (live) {
+      const int j = b.n == 1 ? 0 : find_router(b, v);
+      w = __ldcs(b.vec[j] + (v - b.prefix[j]));
+      jb = (uint64_t)j * count;
+    }
+    touch_pair<COMBINE>(bits, jb, w.x, w.y, live, sT, d, r0, r1, se0, count);
+    touch_pair<COMBINE>(bits, jb, w.z, w.w, live, sT, d, r0, r1, se0, count);
   }
 }
 
@@ -162,27 +175,30 @@ __global__ void __launch_bounds__(kBlock) k_prehash(const Dims d, const uint32_t
   }
 }
 
+template <int U, bool COMBINE>
 __global__ void __launch_bounds__(kBlock) k_touch_packed(const Dims d, const uint4* __restrict__ vec, uint64_t nvec,
                                                          const uint2* __restrict__ tail, uint32_t* __restrict__ bits,
                                                          uint64_t se0, uint64_t count) {
   const uint32_t r0 = (uint32_t)(se0 >> d.q), r1 = (uint32_t)((se0 + count - 1) >> d.q);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && tail) touch_packed(bits, tail->x, tail->y, d, r0, r1, se0, count);
+  const uint32_t lane = threadIdx.x & 31u;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && tail) touch_packed<false>(bits, tail->x, tail->y, true, d, r0, r1, se0, count);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; v + (kUnroll - 1) * stride < nvec; v += kUnroll * stride) {
-    uint4 w[kUnroll];
+  uint64_t vb = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);  // as in k_touch
+  for (; vb + 31 + (U - 1) * stride < nvec; vb += U * stride) {
+    uint4 w[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) w[u] = __ldcs(vec + v + u * stride);
+    for (int u = 0; u < U; ++u) w[u] = __ldcs(vec + vb + lane + u * stride);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      touch_packed(bits, w[u].x, w[u].y, d, r0, r1, se0, count);
-      touch_packed(bits, w[u].z, w[u].w, d, r0, r1, se0, count);
+    for (int u = 0; u < U; ++u) {
+      touch_packed<COMBINE>(bits, w[u].x, w[u].y, true, d, r0, r1, se0, count);
+      touch_packed<COMBINE>(bits, w[u].z, w[u].w, true, d, r0, r1, se0, count);
     }
   }
-  for (; v < nvec; v += stride) {
-    const uint4 w = __ldcs(vec + v);
-    touch_packed(bits, w.x, w.y, d, r0, r1, se0, count);
-    touch_packed(bits, w.z, w.w, d, r0, r1, se0, count);
+  for (; vb < nvec; vb += stride) {
+    const bool live = vb + lane < nvec;
+    const uint4 w = live ? __ldcs(vec + vb + lane) : make_uint4(0, 0, 0, 0);
+    touch_packed<COMBINE>(bits, w.x, w.y, live, d, r0, r1, se0, count);
+    touch_packed<COMBINE>(bits, w.z, w.w, live, d, r0, r1, se0, count);
   }
 }
 
@@ -194,21 +210,44 @@ cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatc
   return cudaGetLastError();
 }
 
+// Instantiates F<U, C> for the tuning's unroll and combine choice.
+#define SSD_TUNED_LAUNCH(KERNEL, GRID, SMEM, ST, ...)                                   \
+  do {                                                                                  \
+    const bool c_ = tn.combine != 0;                                                    \
+    switch (tn.unroll) {                                                                \
+      case 1: if (c_) KERNEL<1, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
+              else KERNEL<1, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
+      case 2: if (c_) KERNEL<2, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
+              else KERNEL<2, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
+      case 8: if (c_) KERNEL<8, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
+              else KERNEL<8, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
+      default: if (c_) KERNEL<4, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);        \
+               else KERNEL<4, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;   \
+    }                                                                                   \
+  } while (0)
+
 cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
-                                uint64_t se0, uint64_t se_count, int grid, cudaStream_t st) {
-  k_touch_packed<<<grid, kBlock, 0, st>>>(d, vec, nvec, tail, bits, se0, se_count);
+                                uint64_t se0, uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st) {
+  SSD_TUNED_LAUNCH(k_touch_packed, grid, 0, st, d, vec, nvec, tail, bits, se0, se_count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
-                         uint64_t se_count, int grid, cudaStream_t st) {
-  k_touch<<<grid, kBlock, 0, st>>>(d, tables, b, bits, se0, se_count);
+                         uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st) {
+  SSD_TUNED_LAUNCH(k_touch, grid, 0, st, d, tables, b, bits, se0, se_count);
   return cudaGetLastError();
 }
+#undef SSD_TUNED_LAUNCH
 
-cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, cudaStream_t st) {
+cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, const Tuning& tn,
+                        cudaStream_t st) {
   static_assert(sizeof(ScanBatch) < 32000, "kernel parameter block too large");
-  k_scan<<<grid, kBlock, 0, st>>>(d, tables, b);
+  switch (tn.unroll) {
+    case 1: k_scan<1><<<grid, kBlock, 0, st>>>(d, tables, b); break;
+    case 2: k_scan<2><<<grid, kBlock, 0, st>>>(d, tables, b); break;
+    case 8: k_scan<8><<<grid, kBlock, 0, st>>>(d, tables, b); break;
+    default: k_scan<4><<<grid, kBlock, 0, st>>>(d, tables, b); break;
+  }
   return cudaGetLastError();
 }
 

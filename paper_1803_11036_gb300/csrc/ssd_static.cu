@@ -119,7 +119,7 @@ extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, 
   a.n = 1;
   a.routers[0] = const_cast<uint16_t*>(d_recorders);
   a.global = nullptr;
-  if (ssd::launch_stream(d, s, a, ssd::kHot, sms, st) != cudaSuccess) return SSD_ECUDA;
+  if (ssd::launch_stream(d, s, a, ssd::kHot, sms, ssd::default_tuning(), st) != cudaSuccess) return SSD_ECUDA;
   int launches = 0;
   if (ssd::launch_regain_tail(d, s, d_ips, d_rk, cap, nd, sms, st, &launches) != cudaSuccess) return SSD_ECUDA;
   ssd::DevCounters h;

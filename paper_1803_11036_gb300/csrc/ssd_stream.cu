@@ -127,7 +127,8 @@ __device__ __forceinline__ void pool_if_hot(const Dims& d, const Scratch& s, uin
 }
 
 // eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
-template <bool ONE, bool ADV, bool HOT, bool TOUCH>
+// G (several routers): routers loaded per group before any of them is stored.
+template <bool ONE, bool ADV, bool HOT, bool TOUCH, int G>
 __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) uint8_t smask[];
@@ -151,20 +152,20 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
       for (uint32_t it = 0; it < iters; ++it) {
         const uint64_t at = base + it * 32 + lane;
         uint4 mv = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        // routers in groups of 8: the group's loads are issued before any of its stores
-        for (int n0 = 0; n0 < a.n; n0 += 8) {
-          const int m = a.n - n0 < 8 ? a.n - n0 : 8;
-          uint4 v[8];
-          uint32_t t[8];
+        // routers in groups of G: the group's loads are issued before any of its stores
+        for (int n0 = 0; n0 < a.n; n0 += G) {
+          const int m = a.n - n0 < G ? a.n - n0 : G;
+          uint4 v[G];
+          uint32_t t[G];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < G; ++u) {
             if (u < m) {
               v[u] = __ldcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at);
               if (TOUCH) t[u] = tb[(uint64_t)(n0 + u) * tstride + it * 32];
             }
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < G; ++u) {
             if (u < m) {
               if (TOUCH && t[u]) {
                 v[u] = apply8(v[u], t[u]);
@@ -247,8 +248,10 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
 // estimators of the chunk with their touch bits applied, counts and pools hot
 // ones and advances; with NEXT, between estimators each lane also hashes a share
 // of the slot's pairs and sets the touch bits of the next chunk (L2 atomics that
-// fill the gaps of the memory-bound stream).
-template <bool NEXT, bool PACKED>
+// fill the gaps of the memory-bound stream). The pairs are walked warp by warp
+// (warp e takes vectors e*32 + lane, e*32 + lane + 32*count, ...), so every lane
+// of a warp runs the same iterations, as COMBINE needs.
+template <bool NEXT, bool PACKED, bool COMBINE>
 __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s,
                                                               const __grid_constant__ ChunkArgs a) {
   constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
@@ -267,30 +270,33 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
   uint4* const r0 = reinterpret_cast<uint4*>(a.router);
   uint4* const g = reinterpret_cast<uint4*>(a.global);
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
-  auto touch2 = [&](uint4 w) {
+  auto touch2 = [&](uint4 w, bool live) {
     if (PACKED) {
-      touch_packed(a.next, w.x, w.y, d, nr0, nr1, a.nx_se0, a.nx_count);
-      touch_packed(a.next, w.z, w.w, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_packed<COMBINE>(a.next, w.x, w.y, live, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_packed<COMBINE>(a.next, w.z, w.w, live, d, nr0, nr1, a.nx_se0, a.nx_count);
     } else {
-      touch_pair(a.next, 0, w.x, w.y, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-      touch_pair(a.next, 0, w.z, w.w, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair<COMBINE>(a.next, 0, w.x, w.y, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair<COMBINE>(a.next, 0, w.z, w.w, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
   };
   for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
     const uint64_t se = a.se0 + e;
     uint8_t* tb = a.touch + e * (d.eta >> 3) + lane;
     // this slot's first pair vector is loaded before the estimator so the two loads overlap
-    uint64_t v = e * 32 + lane;
+    const uint64_t vb0 = e * 32;
     uint4 w0 = make_uint4(0, 0, 0, 0);
-    if (NEXT && v < a.nvec) w0 = __ldcs(a.vec + v);
+    if (NEXT && vb0 + lane < a.nvec) w0 = __ldcs(a.vec + vb0 + lane);
     const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, tb, my, lane);
     if (NEXT) {
-      if (v < a.nvec) touch2(w0);
-      for (v += slots; v < a.nvec; v += slots) touch2(__ldcs(a.vec + v));
+      if (vb0 < a.nvec) touch2(w0, vb0 + lane < a.nvec);
+      for (uint64_t vb = vb0 + slots; vb < a.nvec; vb += slots) {
+        const bool live = vb + lane < a.nvec;
+        touch2(live ? __ldcs(a.vec + vb + lane) : make_uint4(0, 0, 0, 0), live);
+      }
       if (e == 0 && lane < 2 && a.edge[lane]) {
         const uint32_t* p = a.edge[lane];
-        if (PACKED) touch_packed(a.next, p[0], p[1], d, nr0, nr1, a.nx_se0, a.nx_count);
-        else touch_pair(a.next, 0, p[0], p[1], sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        if (PACKED) touch_packed<false>(a.next, p[0], p[1], true, d, nr0, nr1, a.nx_se0, a.nx_count);
+        else touch_pair<false>(a.next, 0, p[0], p[1], true, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
       }
     }
     pool_if_hot(d, s, se, cnt, my, lane);
@@ -298,41 +304,50 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
 }
 
 template <typename K>
-int blocks_per_sm(K kernel, size_t smem, int spare) {
+int blocks_per_sm(K kernel, size_t smem, const Tuning& tn) {
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, smem) != cudaSuccess) return 1;
-  b -= spare;
+  if (tn.stream_bps && (int)tn.stream_bps < b) b = (int)tn.stream_bps;
   return b > 0 ? b : 1;
 }
 
+template <bool ONE, bool ADV, bool HOT, bool TOUCH, int G>
+cudaError_t launch_large(const Dims& d, const Scratch& s, const StreamArgs& a, uint64_t count, int sms,
+                         const Tuning& tn, cudaStream_t st) {
+  const size_t smem = HOT ? (size_t)(kBlock / 32) * (d.eta >> 3) : 0;
+  const uint64_t need = (count + (kBlock / 32) - 1) / (kBlock / 32);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_large<ONE, ADV, HOT, TOUCH, G>, smem, tn);
+  if (grid > need) grid = need;
+  k_stream_large<ONE, ADV, HOT, TOUCH, G><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+  return cudaGetLastError();
+}
+
 template <bool ONE, bool ADV, bool HOT, bool TOUCH>
-cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a, int sms, cudaStream_t st,
-                           int spare) {
+cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a, int sms, const Tuning& tn,
+                           cudaStream_t st) {
   const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
   if (d.eta >= 256) {
-    const size_t smem = HOT ? (size_t)(kBlock / 32) * (d.eta >> 3) : 0;
-    const uint64_t need = (count + (kBlock / 32) - 1) / (kBlock / 32);
-    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_large<ONE, ADV, HOT, TOUCH>, smem, spare);
-    if (grid > need) grid = need;
-    k_stream_large<ONE, ADV, HOT, TOUCH><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
-  } else {
-    const uint64_t n_units = count * d.eta / 256;
-    const uint64_t need = (n_units + (kBlock / 32) - 1) / (kBlock / 32);
-    uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_small<ONE, ADV, HOT, TOUCH>, 0, spare);
-    if (grid > need) grid = need;
-    k_stream_small<ONE, ADV, HOT, TOUCH><<<(unsigned)grid, kBlock, 0, st>>>(d, s, a);
+    if (ONE) return launch_large<ONE, ADV, HOT, TOUCH, 1>(d, s, a, count, sms, tn, st);
+    if (tn.group == 2) return launch_large<ONE, ADV, HOT, TOUCH, 2>(d, s, a, count, sms, tn, st);
+    if (tn.group == 4) return launch_large<ONE, ADV, HOT, TOUCH, 4>(d, s, a, count, sms, tn, st);
+    return launch_large<ONE, ADV, HOT, TOUCH, 8>(d, s, a, count, sms, tn, st);
   }
+  const uint64_t n_units = count * d.eta / 256;
+  const uint64_t need = (n_units + (kBlock / 32) - 1) / (kBlock / 32);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_stream_small<ONE, ADV, HOT, TOUCH>, 0, tn);
+  if (grid > need) grid = need;
+  k_stream_small<ONE, ADV, HOT, TOUCH><<<(unsigned)grid, kBlock, 0, st>>>(d, s, a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
-                          cudaStream_t st, int spare_blocks) {
+                          const Tuning& tn, cudaStream_t st) {
   const bool one = a.n == 1, adv = (mode & kAdvance) != 0, hot = (mode & kHot) != 0, touch = a.touch != nullptr;
 #define SSD_STREAM_CASE(O, A, H, T) \
   if (one == O && adv == A && hot == H && touch == T) \
-    return launch_variant<O, A, H, T>(d, s, a, sms, st, spare_blocks);
+    return launch_variant<O, A, H, T>(d, s, a, sms, tn, st);
   SSD_STREAM_CASE(true, true, true, false)
   SSD_STREAM_CASE(true, true, false, false)
   SSD_STREAM_CASE(true, false, true, false)
@@ -347,20 +362,26 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
   return cudaErrorInvalidValue;
 }
 
-template <bool NEXT, bool PACKED>
-cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
+template <bool NEXT, bool PACKED, bool COMBINE>
+cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
+                                 cudaStream_t st) {
   const size_t smem = (size_t)(kBlock / 32) * (d.eta >> 3) + (NEXT && !PACKED ? 2048 * 4 : 0);
   const uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
-  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED>, smem, 0);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED, COMBINE>, smem, tn);
   if (grid > need) grid = need;
-  k_chunk<NEXT, PACKED><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+  k_chunk<NEXT, PACKED, COMBINE><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, cudaStream_t st) {
-  if (!a.next) return launch_chunk_variant<false, false>(d, s, a, sms, st);
-  if (a.packed) return launch_chunk_variant<true, true>(d, s, a, sms, st);
-  return launch_chunk_variant<true, false>(d, s, a, sms, st);
+cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
+                         cudaStream_t st) {
+  if (!a.next) return launch_chunk_variant<false, false, false>(d, s, a, sms, tn, st);
+  if (tn.combine) {
+    if (a.packed) return launch_chunk_variant<true, true, true>(d, s, a, sms, tn, st);
+    return launch_chunk_variant<true, false, true>(d, s, a, sms, tn, st);
+  }
+  if (a.packed) return launch_chunk_variant<true, true, false>(d, s, a, sms, tn, st);
+  return launch_chunk_variant<true, false, false>(d, s, a, sms, tn, st);
 }
 
 }  // namespace ssd

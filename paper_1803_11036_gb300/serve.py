@@ -55,9 +55,15 @@ def device_free_bytes(device: int) -> int:
 
 
 class _Tenant:
-    def __init__(self, params, tables, device, list_cap):
+    def __init__(self, params, tables, device, list_cap, max_slice_pairs=None, tuning=None):
         import torch
         self.ctx = Context(params, tables, device)
+        if tuning:
+            self.ctx.tuning = tuning
+        if max_slice_pairs:
+            # the pre-hash and staging buffers a slice of this size needs, allocated now: a later
+            # slice never grows them, so no cudaFree / cudaMalloc stalls the other tenants' work
+            self.ctx.reserve(max_slice_pairs)
         self.sketch = self.ctx.sketch()
         self.stream = torch.cuda.Stream(torch.device("cuda", device))
         self.slot = 0
@@ -71,7 +77,11 @@ class Server:
     """Request loop over many routers on one GPU."""
 
     def __init__(self, params, tables, device: int = 0, max_inflight: int = 16, list_cap: int = 4096,
-                 reserve_bytes: int = 2 << 30, max_routers: int | None = None, evict_when_done: bool = False):
+                 reserve_bytes: int = 2 << 30, max_routers: int | None = None, evict_when_done: bool = False,
+                 max_slice_pairs: int | None = None, tuning: dict | None = None):
+        """max_slice_pairs: the largest slice a router sends; each admitted router reserves its
+        buffers for it (see Context.reserve). tuning: a launch configuration for every router's
+        context (for instance one picked by Context.autotune on a representative slice)."""
         import torch
         self.params, self.tables, self.device = params, tables, device
         self.max_inflight = max_inflight
@@ -88,13 +98,16 @@ class Server:
         self.admitted_order: list[int] = []
         self.max_routers = max_routers
         self.evict_when_done = evict_when_done
+        self.max_slice_pairs = max_slice_pairs
+        self.tuning = tuning
         self._left: collections.Counter = collections.Counter()   # scheduled slices not yet finished
 
     # ---- admission by device memory
     def bytes_per_router(self) -> int:
         p = self.params
         sketch = p.r << (p.q + p.log2_eta + 1)
-        return int(sketch * 1.1) + (256 << 20)    # RSEA + context scratch (pools, candidate buffers)
+        staged = 24 * (self.max_slice_pairs or 0)   # pre-hashed pairs + two host staging areas
+        return int(sketch * 1.1) + (256 << 20) + staged   # RSEA + context scratch (pools, candidate buffers)
 
     def try_admit(self, router: int) -> bool:
         if router in self.tenants:
@@ -104,7 +117,8 @@ class Server:
         if device_free_bytes(self.device) < self.bytes_per_router() + self.reserve:
             return False
         try:
-            self.tenants[router] = _Tenant(self.params, self.tables, self.device, self.list_cap)
+            self.tenants[router] = _Tenant(self.params, self.tables, self.device, self.list_cap,
+                                           self.max_slice_pairs, self.tuning)
         except SSDError as e:
             if e.code == _abi.SSD_ENOMEM:
                 return False

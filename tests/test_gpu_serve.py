@@ -44,7 +44,10 @@ def run_server(W, slices, **kw):
 def test_alone_equals_mix_and_oracle():
     W = tg.workload("served_small")
     slices = make_slices(W, range(6), 6, mean_gap_s=0.002)
-    mix, _ = run_server(W, slices, max_inflight=4)
+    # the mix reserves every router's buffers for the largest slice and runs another launch
+    # configuration; neither may change a list
+    mix, _ = run_server(W, slices, max_inflight=4, max_slice_pairs=W["traffic"]["count_b"],
+                        tuning=dict(scan_unroll=2, combine_touches=1, touch_chunk_bytes=4 << 20))
     assert len(mix) == len(slices)
     mixd = by_slot(mix)
     for r in (0, 3, 5):
