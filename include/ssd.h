@@ -293,10 +293,12 @@ SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
  *       (items per thread per step: 1, 2, 4 or 8);
  *   merge_group: routers whose recorders one lane loads before it stores any
  *       of them in the multi-router streaming pass (the merge tile: 2, 4 or 8);
- *   combine_touches: 1 = the lanes of a warp whose touch bits fall into one
- *       32-bit word OR them together (__match_any_sync) and issue one atomic,
- *       which helps when a few sources send much of the traffic; 0 = one
- *       atomic per touch. */
+ *   combine_touches: how touches that land on one 32-bit word of the touch
+ *       bits are combined. 0 = one atomic per touch; 1 = the lanes of a warp
+ *       whose bits fall into one word OR them together (__match_any_sync) and
+ *       issue one atomic; 2 = the word is read from L2 first and the atomic is
+ *       skipped when the bit is already set, which removes the repeats of a
+ *       source that sends many packets to few peers. */
 typedef struct ssd_tuning {
   uint64_t touch_chunk_bytes;
   uint32_t stream_blocks_per_sm;

@@ -847,7 +847,7 @@ int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
   const uint32_t u = t->scan_unroll, g = t->merge_group;
   if (u != 1 && u != 2 && u != 4 && u != 8) return SSD_EINVAL;
   if (g != 2 && g != 4 && g != 8) return SSD_EINVAL;
-  if (t->combine_touches > 1) return SSD_EINVAL;
+  if (t->combine_touches > 2) return SSD_EINVAL;
   const uint64_t bytes = (t->touch_chunk_bytes + 255) & ~255ull;
   if (bytes != ctx->touch_bytes) {  // new touch buffers, zeroed, before the old ones go
     DeviceGuard dg(ctx->device);
@@ -938,7 +938,7 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
         case 2: for (uint64_t b : {2ull, 4ull, 8ull, 16ull, 32ull}) cand[nc++] = b; break;
         case 3: for (uint64_t u : {1ull, 2ull, 4ull, 8ull}) cand[nc++] = u; break;
         case 4: if (n > 1) for (uint64_t g : {2ull, 4ull, 8ull}) cand[nc++] = g; break;
-        default: for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
+        default: for (uint64_t c : {0ull, 1ull, 2ull}) cand[nc++] = c; break;
       }
       auto with = [&](uint64_t v) {
         ssd_tuning t = best;

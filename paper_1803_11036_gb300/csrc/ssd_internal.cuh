@@ -53,7 +53,7 @@ struct Tuning {
   uint32_t scan_bps;     // scan / touch / pre-hash grid = SMs x scan_bps at most
   uint32_t unroll;       // pair vectors per thread per step: 1, 2, 4, 8
   uint32_t group;        // routers loaded per lane before storing, multi-router pass: 2, 4, 8
-  uint32_t combine;      // combine same-word touch atomics inside a warp
+  uint32_t combine;      // how same-word touch atomics are combined (set_touch's CM)
 };
 inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u}; }
 
@@ -105,18 +105,33 @@ __device__ __forceinline__ uint32_t tab_hash(const uint32_t* T, uint32_t x) {
   return T[x & 255u] ^ T[256u + ((x >> 8) & 255u)] ^ T[512u + ((x >> 16) & 255u)] ^ T[768u + (x >> 24)];
 }
 
-// Sets bit `bit` of `bits` (an L2-resident touch buffer) when ok. With COMBINE
-// all 32 lanes of the warp must make the call together: lanes whose bits fall
-// into one 32-bit word are grouped (__match_any_sync on the word index), the
-// group ORs its bits (__reduce_or_sync over the group's mask) and its lowest
-// lane issues the one atomic. Lanes with ok == false join with a key no word has.
-template <bool COMBINE>
+// Sets bit `bit` of `bits` (an L2-resident touch buffer) when ok. CM picks how
+// touches that land on one word are combined:
+//  0: one atomicOr per touch;
+//  1: inside the warp: lanes whose bits fall into one 32-bit word are grouped
+//     (__match_any_sync on the word index), the group ORs its bits
+//     (__reduce_or_sync over the group's mask) and its lowest lane issues the
+//     one atomic. All 32 lanes must make the call together; a lane with
+//     ok == false joins with a key no word has;
+//  2: across the GPU: the word is read from L2 first (ld.global.cg) and the
+//     atomic is skipped when the bit is already set. Bits are only set while a
+//     buffer is collected (it was cleared by an earlier launch on the same
+//     stream order), so a stale read can only cost a redundant atomic. A source
+//     sending many packets to few peers sets each of its bits thousands of
+//     times per slot; this drops those repeats.
+template <int CM>
 __device__ __forceinline__ void set_touch(uint32_t* bits, uint64_t bit, bool ok) {
-  if (COMBINE) {
+  if (CM == 1) {
     const unsigned long long word = ok ? (unsigned long long)(bit >> 5) : ~0ull;
     const unsigned grp = __match_any_sync(0xFFFFFFFFu, word);
     const unsigned v = __reduce_or_sync(grp, ok ? (1u << (bit & 31u)) : 0u);
     if (ok && (threadIdx.x & 31u) == (unsigned)(__ffs(grp) - 1)) atomicOr(bits + word, v);
+  } else if (CM == 2) {
+    if (ok) {
+      uint32_t* w = bits + (bit >> 5);
+      const uint32_t m = 1u << (bit & 31u);
+      if (!(__ldcg(w) & m)) atomicOr(w, m);
+    }
   } else if (ok) {
     atomicOr(bits + (bit >> 5), 1u << (bit & 31u));
   }
@@ -126,9 +141,9 @@ __device__ __forceinline__ void set_touch(uint32_t* bits, uint64_t bit, bool ok)
 // row or whole rows): the recorder a pair sets to 0 is marked in `bits` instead
 // (router base jbase = router * count; estimator se0 + e, recorder x -> bit
 // (jbase + e) * eta + x). sT holds both table sets (2048 words). `live` = false
-// makes the call a no-op (a lane past the end of the pairs; with COMBINE every
+// makes the call a no-op (a lane past the end of the pairs; with CM == 1 every
 // lane calls).
-template <bool COMBINE>
+template <int CM>
 __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint32_t cip, uint32_t oip, bool live,
                                            const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
                                            uint64_t se0, uint64_t count) {
@@ -143,12 +158,12 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
     const bool ok = live && e < count;
     if (ok && x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
-    set_touch<COMBINE>(bits, ((jbase + e) << d.log2_eta) | x, ok);
+    set_touch<CM>(bits, ((jbase + e) << d.log2_eta) | x, ok);
   }
 }
 
 // touch_pair on a pre-hashed pair: packed = RHFG[0](cip) | H1(oip) << q (q + log2_eta <= 32).
-template <bool COMBINE>
+template <int CM>
 __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint32_t packed, bool live, const Dims& d,
                                              uint32_t r0, uint32_t r1, uint64_t se0, uint64_t count) {
   const uint32_t c0 = packed & d.col_mask;
@@ -160,7 +175,7 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    set_touch<COMBINE>(bits, (e << d.log2_eta) | x, live && e < count);
+    set_touch<CM>(bits, (e << d.log2_eta) | x, live && e < count);
   }
 }
 

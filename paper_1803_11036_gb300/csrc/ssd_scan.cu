@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
 
 // The touch kernels walk the vectors warp by warp (vb = the warp's first
 // vector, a multiple of 32 because the grid stride is): every lane of a warp
-// runs the same iterations, as set_touch<true> needs; a lane past the end only
+// runs the same iterations, as set_touch<1> needs; a lane past the end only
 // takes part.
-template <int U, bool COMBINE>
+template <int U, int CM>
 __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* __restrict__ tables,
                                                   const __grid_constant__ ScanBatch b, uint32_t* __restrict__ bits,
                                                   uint64_t se0, uint64_t count) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
   const uint32_t lane = threadIdx.x & 31u;
   if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
     const uint32_t* e = b.edge[threadIdx.x];
-    if (e) touch_pair<false>(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], true, sT, d, r0, r1, se0, count);
+    if (e) touch_pair<0>(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], true, sT, d, r0, r1, se0, count);
   }
   const uint64_t total = b.prefix[b.n];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      touch_pair<COMBINE>(bits, jb[u], w[u].x, w[u].y, true, sT, d, r0, r1, se0, count);
-      touch_pair<COMBINE>(bits, jb[u], w[u].z, w[u].w, true, sT, d, r0, r1, se0, count);
+      touch_pair<CM>(bits, jb[u], w[u].x, w[u].y, true, sT, d, r0, r1, se0, count);
+      touch_pair<CM>(bits, jb[u], w[u].z, w[u].w, true, sT, d, r0, r1, se0, count);
     }
   }
   for (; vb < total; vb += stride) {
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
       w = __ldcs(b.vec[j] + (v - b.prefix[j]));
       jb = (uint64_t)j * count;
     }
-    touch_pair<COMBINE>(bits, jb, w.x, w.y, live, sT, d, r0, r1, se0, count);
-    touch_pair<COMBINE>(bits, jb, w.z, w.w, live, sT, d, r0, r1, se0, count);
+    touch_pair<CM>(bits, jb, w.x, w.y, live, sT, d, r0, r1, se0, count);
+    touch_pair<CM>(bits, jb, w.z, w.w, live, sT, d, r0, r1, se0, count);
   }
 }
 
@@ -175,13 +175,13 @@ __global__ void __launch_bounds__(kBlock) k_prehash(const Dims d, const uint32_t
   }
 }
 
-template <int U, bool COMBINE>
+template <int U, int CM>
 __global__ void __launch_bounds__(kBlock) k_touch_packed(const Dims d, const uint4* __restrict__ vec, uint64_t nvec,
                                                          const uint2* __restrict__ tail, uint32_t* __restrict__ bits,
                                                          uint64_t se0, uint64_t count) {
   const uint32_t r0 = (uint32_t)(se0 >> d.q), r1 = (uint32_t)((se0 + count - 1) >> d.q);
   const uint32_t lane = threadIdx.x & 31u;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && tail) touch_packed<false>(bits, tail->x, tail->y, true, d, r0, r1, se0, count);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && tail) touch_packed<0>(bits, tail->x, tail->y, true, d, r0, r1, se0, count);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t vb = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);  // as in k_touch
   for (; vb + 31 + (U - 1) * stride < nvec; vb += U * stride) {
@@ -190,15 +190,15 @@ __global__ void __launch_bounds__(kBlock) k_touch_packed(const Dims d, const uin
     for (int u = 0; u < U; ++u) w[u] = __ldcs(vec + vb + lane + u * stride);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      touch_packed<COMBINE>(bits, w[u].x, w[u].y, true, d, r0, r1, se0, count);
-      touch_packed<COMBINE>(bits, w[u].z, w[u].w, true, d, r0, r1, se0, count);
+      touch_packed<CM>(bits, w[u].x, w[u].y, true, d, r0, r1, se0, count);
+      touch_packed<CM>(bits, w[u].z, w[u].w, true, d, r0, r1, se0, count);
     }
   }
   for (; vb < nvec; vb += stride) {
     const bool live = vb + lane < nvec;
     const uint4 w = live ? __ldcs(vec + vb + lane) : make_uint4(0, 0, 0, 0);
-    touch_packed<COMBINE>(bits, w.x, w.y, live, d, r0, r1, se0, count);
-    touch_packed<COMBINE>(bits, w.z, w.w, live, d, r0, r1, se0, count);
+    touch_packed<CM>(bits, w.x, w.y, live, d, r0, r1, se0, count);
+    touch_packed<CM>(bits, w.z, w.w, live, d, r0, r1, se0, count);
   }
 }
 
@@ -210,34 +210,36 @@ cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatc
   return cudaGetLastError();
 }
 
-// Instantiates F<U, C> for the tuning's unroll and combine choice.
-#define SSD_TUNED_LAUNCH(KERNEL, GRID, SMEM, ST, ...)                                   \
-  do {                                                                                  \
-    const bool c_ = tn.combine != 0;                                                    \
-    switch (tn.unroll) {                                                                \
-      case 1: if (c_) KERNEL<1, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
-              else KERNEL<1, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
-      case 2: if (c_) KERNEL<2, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
-              else KERNEL<2, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
-      case 8: if (c_) KERNEL<8, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);         \
-              else KERNEL<8, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;    \
-      default: if (c_) KERNEL<4, true><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__);        \
-               else KERNEL<4, false><<<GRID, kBlock, SMEM, ST>>>(__VA_ARGS__); break;   \
-    }                                                                                   \
+// Launches KERNEL<U, CM> for the tuning's unroll (U) and combine mode (CM).
+#define SSD_TUNED_CM(KERNEL, U, GRID, ST, ...)                                             \
+  do {                                                                                    \
+    if (tn.combine == 1) KERNEL<U, 1><<<GRID, kBlock, 0, ST>>>(__VA_ARGS__);             \
+    else if (tn.combine == 2) KERNEL<U, 2><<<GRID, kBlock, 0, ST>>>(__VA_ARGS__);        \
+    else KERNEL<U, 0><<<GRID, kBlock, 0, ST>>>(__VA_ARGS__);                             \
+  } while (0)
+#define SSD_TUNED_LAUNCH(KERNEL, GRID, ST, ...)                                           \
+  do {                                                                                    \
+    switch (tn.unroll) {                                                                  \
+      case 1: SSD_TUNED_CM(KERNEL, 1, GRID, ST, __VA_ARGS__); break;                      \
+      case 2: SSD_TUNED_CM(KERNEL, 2, GRID, ST, __VA_ARGS__); break;                      \
+      case 8: SSD_TUNED_CM(KERNEL, 8, GRID, ST, __VA_ARGS__); break;                      \
+      default: SSD_TUNED_CM(KERNEL, 4, GRID, ST, __VA_ARGS__); break;                     \
+    }                                                                                     \
   } while (0)
 
 cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
                                 uint64_t se0, uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st) {
-  SSD_TUNED_LAUNCH(k_touch_packed, grid, 0, st, d, vec, nvec, tail, bits, se0, se_count);
+  SSD_TUNED_LAUNCH(k_touch_packed, grid, st, d, vec, nvec, tail, bits, se0, se_count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_touch(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint32_t* bits, uint64_t se0,
                          uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st) {
-  SSD_TUNED_LAUNCH(k_touch, grid, 0, st, d, tables, b, bits, se0, se_count);
+  SSD_TUNED_LAUNCH(k_touch, grid, st, d, tables, b, bits, se0, se_count);
   return cudaGetLastError();
 }
 #undef SSD_TUNED_LAUNCH
+#undef SSD_TUNED_CM
 
 cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, const Tuning& tn,
                         cudaStream_t st) {

@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
 // of the slot's pairs and sets the touch bits of the next chunk (L2 atomics that
 // fill the gaps of the memory-bound stream). The pairs are walked warp by warp
 // (warp e takes vectors e*32 + lane, e*32 + lane + 32*count, ...), so every lane
-// of a warp runs the same iterations, as COMBINE needs.
-template <bool NEXT, bool PACKED, bool COMBINE>
+// of a warp runs the same iterations, as combine mode 1 needs.
+template <bool NEXT, bool PACKED, int CM>
 __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s,
                                                               const __grid_constant__ ChunkArgs a) {
   constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
@@ -272,11 +272,11 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
   auto touch2 = [&](uint4 w, bool live) {
     if (PACKED) {
-      touch_packed<COMBINE>(a.next, w.x, w.y, live, d, nr0, nr1, a.nx_se0, a.nx_count);
-      touch_packed<COMBINE>(a.next, w.z, w.w, live, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_packed<CM>(a.next, w.x, w.y, live, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_packed<CM>(a.next, w.z, w.w, live, d, nr0, nr1, a.nx_se0, a.nx_count);
     } else {
-      touch_pair<COMBINE>(a.next, 0, w.x, w.y, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-      touch_pair<COMBINE>(a.next, 0, w.z, w.w, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair<CM>(a.next, 0, w.x, w.y, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair<CM>(a.next, 0, w.z, w.w, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
   };
   for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
       }
       if (e == 0 && lane < 2 && a.edge[lane]) {
         const uint32_t* p = a.edge[lane];
-        if (PACKED) touch_packed<false>(a.next, p[0], p[1], true, d, nr0, nr1, a.nx_se0, a.nx_count);
-        else touch_pair<false>(a.next, 0, p[0], p[1], true, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        if (PACKED) touch_packed<0>(a.next, p[0], p[1], true, d, nr0, nr1, a.nx_se0, a.nx_count);
+        else touch_pair<0>(a.next, 0, p[0], p[1], true, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
       }
     }
     pool_if_hot(d, s, se, cnt, my, lane);
@@ -362,26 +362,28 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
   return cudaErrorInvalidValue;
 }
 
-template <bool NEXT, bool PACKED, bool COMBINE>
+template <bool NEXT, bool PACKED, int CM>
 cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                                  cudaStream_t st) {
   const size_t smem = (size_t)(kBlock / 32) * (d.eta >> 3) + (NEXT && !PACKED ? 2048 * 4 : 0);
   const uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
-  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED, COMBINE>, smem, tn);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED, CM>, smem, tn);
   if (grid > need) grid = need;
-  k_chunk<NEXT, PACKED, COMBINE><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
+  k_chunk<NEXT, PACKED, CM><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st) {
-  if (!a.next) return launch_chunk_variant<false, false, false>(d, s, a, sms, tn, st);
-  if (tn.combine) {
-    if (a.packed) return launch_chunk_variant<true, true, true>(d, s, a, sms, tn, st);
-    return launch_chunk_variant<true, false, true>(d, s, a, sms, tn, st);
+  if (!a.next) return launch_chunk_variant<false, false, 0>(d, s, a, sms, tn, st);
+  if (a.packed) {
+    if (tn.combine == 1) return launch_chunk_variant<true, true, 1>(d, s, a, sms, tn, st);
+    if (tn.combine == 2) return launch_chunk_variant<true, true, 2>(d, s, a, sms, tn, st);
+    return launch_chunk_variant<true, true, 0>(d, s, a, sms, tn, st);
   }
-  if (a.packed) return launch_chunk_variant<true, true, false>(d, s, a, sms, tn, st);
-  return launch_chunk_variant<true, false, false>(d, s, a, sms, tn, st);
+  if (tn.combine == 1) return launch_chunk_variant<true, false, 1>(d, s, a, sms, tn, st);
+  if (tn.combine == 2) return launch_chunk_variant<true, false, 2>(d, s, a, sms, tn, st);
+  return launch_chunk_variant<true, false, 0>(d, s, a, sms, tn, st);
 }
 
 }  // namespace ssd

@@ -21,6 +21,8 @@ TUNINGS = [
          combine_touches=1),
     dict(touch_chunk_bytes=16 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=1, scan_unroll=2, merge_group=8,
          combine_touches=0),
+    dict(touch_chunk_bytes=8 << 20, stream_blocks_per_sm=3, scan_blocks_per_sm=4, scan_unroll=4, merge_group=8,
+         combine_touches=2),
 ]
 
 
@@ -73,7 +75,7 @@ def test_tuning_rejects_bad_values():
     assert before == dict(touch_chunk_bytes=32 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=8, scan_unroll=4,
                           merge_group=8, combine_touches=0)
     for bad in (dict(scan_unroll=3), dict(merge_group=1), dict(scan_blocks_per_sm=0), dict(scan_blocks_per_sm=33),
-                dict(stream_blocks_per_sm=9), dict(combine_touches=2), dict(touch_chunk_bytes=1 << 10),
+                dict(stream_blocks_per_sm=9), dict(combine_touches=3), dict(touch_chunk_bytes=1 << 10),
                 dict(touch_chunk_bytes=2 << 30)):
         with pytest.raises(ssd.SSDError) as e:
             ctx.tuning = bad
