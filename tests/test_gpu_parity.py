@@ -336,3 +336,27 @@ def test_checkpoint_resume_is_bit_identical():
         assert np.array_equal(x.export(), y.export()) and x.slot == y.slot
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("step", ["slot", "fused", "unfused"])
+def test_discrete_window_k1(step):
+    """k = 1, the discrete-window case of the sliding estimator: a recorder counts only in the slot
+    that touched it, so each slot's list depends on that slot's pairs alone. The planted hosts send
+    all their peers in every slot (pacing D/k with k = 1)."""
+    W = tg.workload("paper_c1")
+    W["params"]["k"] = 1
+    W["traffic"]["k"] = 1
+    run = Run(W)
+    nonempty = 0
+    for _ in range(5):
+        if step == "slot":
+            got, want = run.step_slot("pruned", with_global=True)
+        elif step == "fused":
+            got, want = run.step_fused("pruned")
+        else:
+            got, want = run.step_unfused("pruned")
+        assert_list_equal(got, want, f"slot {run.t}")
+        assert np.array_equal(run.glob.export(), run.pipe.global_sk), run.t
+        nonempty += len(want["ips"]) > 0
+    assert nonempty == 5
+    run.close()

@@ -82,3 +82,58 @@ def test_admission_waits_for_memory():
     assert a.keys() == b.keys()
     for key in a:
         assert np.array_equal(a[key][0], b[key][0]) and np.array_equal(a[key][1], b[key][1]), key
+
+
+def test_served_full_size_sampled():
+    """Three routers of the served workload at full size (q = 17, slices of 10k-2M packets) through
+    the Server in the bench's configuration (16 in flight, buffers reserved for 2M-packet slices).
+    With the RHFG[0] check on, each router's list of every slot is decided by a sample of its
+    estimators, which the oracle follows through every packet; the router's sketch after its last
+    slice is checked on the same sample."""
+    W = tg.workload("served_c5")
+    tabs = tg.hash_tables(W["hash_seed"])
+    routers = range(3)
+    slices = make_slices(W, routers, 5, mean_gap_s=0.001, seed=3)
+    params = ssd.make_params(W["params"], ssd.SSD_VERIFY_H0)
+    srv = serve.Server(params, tabs, max_inflight=16, max_slice_pairs=W["traffic"]["count_b"])
+    res = srv.run(slices)
+    got = by_slot(res)
+    p = oracle.params(W["params"], oracle.VERIFY_H0)
+    thr, _ = oracle.threshold(p.eta, p.theta)
+    rng = np.random.default_rng(9)
+    members = 0
+    for r in routers:
+        tr = dict(W["traffic"])
+        tr["seed"] = tr["seed"] + 101 * r
+        T = tg.Traffic(**tr)
+        mine = sorted([s for s in slices if s.router == r], key=lambda s: s.seq)
+        hosts = set(T.planted_ips().tolist())
+        hosts |= {T.lib.tg_src_ip(T._h, int(x)) for x in rng.integers(0, tr["n_src"], 100)}
+        for s in mine:
+            hosts |= set(got[(r, s.seq)][0].tolist())
+        hosts = sorted(hosts)
+        cols = {x: oracle.rhfg(p, tabs, x) for x in hosts}
+        rows = np.concatenate([np.arange(p.r, dtype=np.uint32) for _ in hosts])
+        cc = np.concatenate([cols[x].astype(np.uint32) for x in hosts])
+        samp = oracle.Sampled(p, rows, cc)
+        for s in mine:
+            if s.seq:
+                samp.advance()
+            samp.scan(tabs, s.pairs.numpy().view(np.uint32).reshape(-1, 2))
+            listed = dict(zip(got[(r, s.seq)][0].tolist(), got[(r, s.seq)][1].tolist()))
+            for x in hosts:
+                below = [samp.get(i, int(cols[x][i])) < p.k for i in range(p.r)]
+                union = int(np.logical_and.reduce(below).sum())
+                member = all(int(b.sum()) >= thr for b in below) and union >= thr
+                assert (x in listed) == member, (r, s.seq, hex(x))
+                if member:
+                    assert listed[x] == union
+                    members += 1
+        samp.advance()
+        sk = srv.tenants[r].sketch
+        for i in range(p.r):
+            c = int(cols[hosts[0]][i])
+            assert np.array_equal(sk.export_estimator(i, c), samp.get(i, c)), (r, i)
+        samp.close()
+    assert members > 0
+    srv.close()
