@@ -21,6 +21,9 @@ struct ssd_ctx {
   uint32_t* ctb[2];
   unsigned long long* stage;
   ssd::DevCounters* counters;
+  uint32_t* bucket_off;
+  uint32_t* bucket_cnt;
+  uint32_t* bucket_ent;
   unsigned long long* n_out;  // list size of ssd_regain
   uint64_t launches;
   // tracing events (caller-owned)
@@ -207,6 +210,9 @@ void free_ctx(ssd_ctx* c) {
   cudaFree(c->ctb[1]);
   cudaFree(c->stage);
   cudaFree(c->counters);
+  cudaFree(c->bucket_off);
+  cudaFree(c->bucket_cnt);
+  cudaFree(c->bucket_ent);
   cudaFree(c->n_out);
   delete c;
 }
@@ -283,6 +289,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   d.out_cap = pow2_at_least(p->out_capacity ? p->out_capacity : (1ull << 20));
 
   const uint64_t R = p->r;
+  const uint64_t NB = d.low_bits <= ssd::kMaxBucketBits ? (1ull << d.low_bits) : 0;  // 0: no bucket index
   c->touch_bytes = p->touch_chunk_bytes ? p->touch_chunk_bytes : (32ull << 20);
   c->touch_bytes = (c->touch_bytes + 255) & ~255ull;
   struct Alloc { void** ptr; uint64_t bytes; } allocs[] = {
@@ -298,6 +305,9 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
       {(void**)&c->stage, d.out_cap * 8},
       {(void**)&c->counters, sizeof(ssd::DevCounters)},
       {(void**)&c->n_out, 8},
+      {(void**)&c->bucket_off, NB ? R * (NB + 1) * 4 : 0},
+      {(void**)&c->bucket_cnt, NB ? R * NB * 4 : 0},
+      {(void**)&c->bucket_ent, NB ? R * d.hse_cap * 4 : 0},
   };
   for (auto& a : allocs) {
     if (a.bytes == 0) continue;
@@ -329,6 +339,9 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   c->s.ctb[1] = c->ctb[1];
   c->s.stage = c->stage;
   c->s.counters = c->counters;
+  c->s.bucket_off = c->bucket_off;
+  c->s.bucket_cnt = c->bucket_cnt;
+  c->s.bucket_ent = c->bucket_ent;
   *out = c;
   return SSD_OK;
 }

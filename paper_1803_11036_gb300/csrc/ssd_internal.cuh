@@ -44,7 +44,16 @@ struct Scratch {
   uint32_t* ctb[2];         // candidate tuple buffers, tuple stride r (pool indices)
   unsigned long long* stage;  // [out_cap] (cip << 32) | R_k of accepted tuples
   DevCounters* counters;
+  // Per row, the pooled hot estimators bucketed by the low q-delta bits of their
+  // column (the bits the overlap test fixes): bucket_off [r][2^(q-delta) + 1]
+  // offsets into bucket_ent [r][hse_cap] (pool indices); bucket_cnt [r][2^(q-delta)]
+  // is the build's work space. nullptr: the candidate levels probe hot_idx.
+  uint32_t* bucket_off;
+  uint32_t* bucket_cnt;
+  uint32_t* bucket_ent;
 };
+// Largest q - delta for which a context keeps the bucket index.
+constexpr uint32_t kMaxBucketBits = 16;
 
 // Launch configuration (ssd_tuning without the touch buffer size). No field
 // changes a result; each one only spreads the same work differently.

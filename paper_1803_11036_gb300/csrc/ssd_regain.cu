@@ -8,10 +8,13 @@
 //   a dropped tuple would fail the final test. Computed as a 32 x 32 tile of
 //   AND-popcounts per block with the bitmaps staged in shared memory.
 // Level i >= 2: the overlap test fixes the low q-delta bits of he_i
-//   (B(i) mod 2^(q-delta) = B(i-1) >> delta with B(j) = he_0 XOR he_j), so each
-//   candidate needs only 2^delta probes of row i instead of a scan of HSE(i);
-//   probes that hit a hot estimator are tested by the whole warp (coalesced
-//   bitmap reads) and survivors are appended with warp-aggregated atomics.
+//   (B(i) mod 2^(q-delta) = B(i-1) >> delta with B(j) = he_0 XOR he_j), so the
+//   only row-i estimators a candidate can extend to are the hot ones with those
+//   low bits. The k_pairs launch also buckets each row's hot estimators by their
+//   low q-delta bits, and a candidate reads its one bucket (when 2^(q-delta) is
+//   too large for the index, it probes the 2^delta columns in hot_idx instead).
+//   Hits are tested by the whole warp (coalesced bitmap reads) and survivors
+//   are appended with warp-aggregated atomics.
 // The last level applies the final test (R_k of the full union), regains the
 //   host from B(1..r-1) and stages (cip, R_k); one block then sorts the staged
 //   entries and writes the ascending, duplicate-free list.
@@ -58,9 +61,56 @@ __device__ __forceinline__ bool regain_host(const Dims& d, const uint32_t* he, u
   return true;
 }
 
+// Row i's pooled hot estimators bucketed by the low q-delta bits of their column
+// (one block; counting sort in global memory: count, exclusive scan, fill). The
+// order inside a bucket is that of the fill's atomics; the levels do not depend
+// on it (the list is sorted at the end).
+__device__ void build_buckets(const Dims& d, const Scratch& s, uint32_t i) {
+  __shared__ uint32_t part[kBlock];
+  const uint32_t nb = 1u << d.low_bits;
+  uint32_t* off = s.bucket_off + (uint64_t)i * (nb + 1);
+  uint32_t* cnt = s.bucket_cnt + (uint64_t)i * nb;
+  uint32_t* ent = s.bucket_ent + (uint64_t)i * d.hse_cap;
+  const uint32_t* col = s.pool_col + (uint64_t)i * d.hse_cap;
+  const uint32_t n = min(s.counters->hot[i], d.hse_cap);
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) atomicAdd(&cnt[col[j] & d.low_mask], 1u);
+  __syncthreads();
+  // exclusive scan: each thread sums a contiguous segment, the block scans the sums
+  const uint32_t seg = (nb + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(threadIdx.x * seg, nb), hi = min(lo + seg, nb);
+  uint32_t sum = 0;
+  for (uint32_t b = lo; b < hi; ++b) sum += cnt[b];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (uint32_t o = 1; o < blockDim.x; o <<= 1) {   // inclusive Hillis-Steele scan of the sums
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (uint32_t b = lo; b < hi; ++b) {
+    const uint32_t c = cnt[b];
+    off[b] = run;
+    cnt[b] = run;   // the fill's cursor
+    run += c;
+  }
+  if (threadIdx.x == blockDim.x - 1) off[nb] = part[blockDim.x - 1];
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) ent[atomicAdd(&cnt[col[j] & d.low_mask], 1u)] = j;
+}
+
 constexpr int TA = 32, KW = 64;
 
-__global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s) {
+// Blocks [0, pair_blocks) test the pairs; with the bucket index, block
+// pair_blocks + m builds the buckets of row 2 + m.
+__global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s, uint32_t pair_blocks) {
+  if (blockIdx.x >= pair_blocks) {
+    build_buckets(d, s, 2 + (blockIdx.x - pair_blocks));
+    return;
+  }
   __shared__ uint32_t A[TA][KW + 1], B[TA][KW + 1];
   const uint32_t n0 = min(s.counters->hot[0], d.hse_cap);
   const uint32_t n1 = min(s.counters->hot[1], d.hse_cap);
@@ -70,7 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const uint32_t* bm0 = s.pool_bm;
   const uint32_t* bm1 = s.pool_bm + (uint64_t)d.hse_cap * d.words;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (uint64_t t = blockIdx.x; t < ntiles; t += pair_blocks) {
     const uint32_t a0 = (uint32_t)(t / t1) * TA, b0 = (uint32_t)(t % t1) * TA;
     uint32_t acc[2][2] = {{0, 0}, {0, 0}};
     if (prune) {
@@ -113,81 +163,112 @@ __global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s)
   }
 }
 
+// One candidate tuple c of row level i extended by row-i estimator idx (pool
+// index; kNone when this lane has none): the union test by the whole warp, then
+// the append to the next candidate buffer or, at the last row, the final test,
+// the host and its staging. Every lane of the warp makes the call.
+__device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* rctb,
+                                          uint32_t* sctb, uint64_t c, uint32_t idx, int lane) {
+  const uint64_t cap = d.hse_cap;
+  const bool last = (i == d.r - 1);
+  const bool prune = !(d.flags & SSD_NO_PRUNE);
+  const bool verify = (d.flags & SSD_VERIFY_H0) != 0;
+  const bool hit = idx != kNone;
+  uint32_t pc = 0;
+  if (prune || last) {
+    unsigned m = __ballot_sync(kFull, hit);
+    while (m) {
+      const int L = __ffs(m) - 1;
+      m &= m - 1;
+      const uint64_t cL = __shfl_sync(kFull, c, L);
+      const uint32_t idxL = __shfl_sync(kFull, idx, L);
+      const uint32_t* tL = rctb + cL * d.r;
+      uint32_t sum = 0;
+      for (uint32_t w = lane; w < d.words; w += 32) {
+        uint32_t x = s.pool_bm[((uint64_t)i * cap + idxL) * d.words + w];
+        for (uint32_t j = 0; j < i; ++j) x &= s.pool_bm[((uint64_t)j * cap + tL[j]) * d.words + w];
+        sum += __popc(x);
+      }
+      sum = __reduce_add_sync(kFull, sum);
+      if (lane == L) pc = sum;
+    }
+  }
+  const bool keep = hit && (!prune || pc >= d.thr);
+  if (!last) {
+    const unsigned long long pos = warp_append(keep, &s.counters->level[i]);
+    if (keep) {
+      if (pos < d.ctb_cap) {
+        const uint32_t* tup = rctb + c * d.r;
+        for (uint32_t j = 0; j < i; ++j) sctb[pos * d.r + j] = tup[j];
+        sctb[pos * d.r + i] = idx;
+      } else {
+        atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
+      }
+    }
+  } else {
+    warp_append(keep, &s.counters->level[i]);
+    bool acc = hit && pc >= d.thr;
+    uint32_t cip = 0;
+    if (acc) {
+      const uint32_t* tup = rctb + c * d.r;
+      uint32_t he[SSD_MAX_R];
+      for (uint32_t j = 0; j < i; ++j) he[j] = s.pool_col[(uint64_t)j * cap + tup[j]];
+      he[i] = s.pool_col[(uint64_t)i * cap + idx];
+      acc = regain_host(d, he, &cip);
+      if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
+    }
+    const unsigned long long pos = warp_append(acc, &s.counters->raw);
+    if (acc) {
+      if (pos < d.out_cap) s.stage[pos] = ((unsigned long long)cip << 32) | pc;
+      else atomicOr(&s.counters->status, SSD_STATUS_OUT_OVERFLOW);
+    }
+  }
+}
+
+// The low q-delta bits the overlap test fixes for row i's estimator of candidate c.
+__device__ __forceinline__ uint32_t fixed_low(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* tup) {
+  const uint32_t he0 = s.pool_col[tup[0]];
+  const uint32_t hep = s.pool_col[(uint64_t)(i - 1) * d.hse_cap + tup[i - 1]];
+  const uint32_t want_low = (he0 ^ hep) >> d.delta;  // high q-delta bits of B(i-1)
+  return (he0 ^ want_low) & d.low_mask;
+}
+
 __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s, const uint32_t i,
                                                   const uint32_t* __restrict__ rctb, uint32_t* __restrict__ sctb) {
   const int lane = threadIdx.x & 31;
   const unsigned long long avail = s.counters->level[i - 1];
   const uint64_t nc = avail < d.ctb_cap ? avail : d.ctb_cap;
-  const uint64_t total = nc << d.delta;
-  const bool last = (i == d.r - 1);
-  const bool prune = !(d.flags & SSD_NO_PRUNE);
-  const bool verify = (d.flags & SSD_VERIFY_H0) != 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t cap = d.hse_cap;
+  if (s.bucket_off) {
+    // one candidate per lane; round p takes each lane's p-th bucket entry
+    const uint32_t nb = 1u << d.low_bits;
+    const uint32_t* off = s.bucket_off + (uint64_t)i * (nb + 1);
+    const uint32_t* ent = s.bucket_ent + (uint64_t)i * d.hse_cap;
+    for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < nc; w0 += stride) {
+      const uint64_t c = w0 + lane;
+      uint32_t b = 0, e = 0;
+      if (c < nc) {
+        const uint32_t low = fixed_low(d, s, i, rctb + c * d.r);
+        b = off[low];
+        e = off[low + 1];
+      }
+      for (uint32_t p = 0; __any_sync(kFull, b + p < e); ++p)
+        level_hit(d, s, i, rctb, sctb, c, b + p < e ? ent[b + p] : kNone, lane);
+    }
+    return;
+  }
+  // probes: 2^delta columns of row i per candidate, one per lane
+  const uint64_t total = nc << d.delta;
   for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < total; w0 += stride) {
     const uint64_t item = w0 + lane;
-    const bool valid = item < total;
     const uint64_t c = item >> d.delta;
     uint32_t idx = kNone;
-    if (valid) {
-      const uint32_t* tup = rctb + c * d.r;
-      const uint32_t he0 = s.pool_col[tup[0]];
-      const uint32_t hep = s.pool_col[(uint64_t)(i - 1) * cap + tup[i - 1]];
-      const uint32_t want_low = ((he0 ^ hep) >> d.delta);  // high q-delta bits of B(i-1)
+    if (item < total) {
       const uint32_t h = (uint32_t)(item & ((1u << d.delta) - 1u));
-      const uint32_t he_i = (h << d.low_bits) | ((he0 ^ want_low) & d.low_mask);
+      const uint32_t he_i = (h << d.low_bits) | fixed_low(d, s, i, rctb + c * d.r);
       idx = s.hot_idx[((uint64_t)i << d.q) | he_i];
     }
-    const bool hit = idx != kNone;
-    uint32_t pc = 0;
-    if (prune || last) {
-      unsigned m = __ballot_sync(kFull, hit);
-      while (m) {
-        const int L = __ffs(m) - 1;
-        m &= m - 1;
-        const uint64_t cL = __shfl_sync(kFull, c, L);
-        const uint32_t idxL = __shfl_sync(kFull, idx, L);
-        const uint32_t* tL = rctb + cL * d.r;
-        uint32_t sum = 0;
-        for (uint32_t w = lane; w < d.words; w += 32) {
-          uint32_t x = s.pool_bm[((uint64_t)i * cap + idxL) * d.words + w];
-          for (uint32_t j = 0; j < i; ++j) x &= s.pool_bm[((uint64_t)j * cap + tL[j]) * d.words + w];
-          sum += __popc(x);
-        }
-        sum = __reduce_add_sync(kFull, sum);
-        if (lane == L) pc = sum;
-      }
-    }
-    const bool keep = hit && (!prune || pc >= d.thr);
-    if (!last) {
-      const unsigned long long pos = warp_append(keep, &s.counters->level[i]);
-      if (keep) {
-        if (pos < d.ctb_cap) {
-          const uint32_t* tup = rctb + c * d.r;
-          for (uint32_t j = 0; j < i; ++j) sctb[pos * d.r + j] = tup[j];
-          sctb[pos * d.r + i] = idx;
-        } else {
-          atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
-        }
-      }
-    } else {
-      warp_append(keep, &s.counters->level[i]);
-      bool acc = hit && pc >= d.thr;
-      uint32_t cip = 0;
-      if (acc) {
-        const uint32_t* tup = rctb + c * d.r;
-        uint32_t he[SSD_MAX_R];
-        for (uint32_t j = 0; j < i; ++j) he[j] = s.pool_col[(uint64_t)j * cap + tup[j]];
-        he[i] = s.pool_col[(uint64_t)i * cap + idx];
-        acc = regain_host(d, he, &cip);
-        if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
-      }
-      const unsigned long long pos = warp_append(acc, &s.counters->raw);
-      if (acc) {
-        if (pos < d.out_cap) s.stage[pos] = ((unsigned long long)cip << 32) | pc;
-        else atomicOr(&s.counters->status, SSD_STATUS_OUT_OVERFLOW);
-      }
-    }
+    level_hit(d, s, i, rctb, sctb, c, idx, lane);
   }
 }
 
@@ -281,7 +362,15 @@ cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, u
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_pairs<<<sms * 2, kBlock, 0, st>>>(d, s);
+  static int pair_bps = 0;   // resident k_pairs blocks per SM
+  if (!pair_bps) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pair_bps, k_pairs, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (pair_bps < 1) pair_bps = 1;
+  }
+  const uint32_t pair_blocks = (uint32_t)(sms * pair_bps);
+  const uint32_t bucket_blocks = s.bucket_off && d.r > 2 ? d.r - 2 : 0;
+  k_pairs<<<pair_blocks + bucket_blocks, kBlock, 0, st>>>(d, s, pair_blocks);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *launches += 1;

@@ -108,6 +108,7 @@ extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, 
   s.ctb[1] = reinterpret_cast<uint32_t*>(b + pl.ctb1);
   s.stage = reinterpret_cast<unsigned long long*>(b + pl.stage);
   s.counters = reinterpret_cast<ssd::DevCounters*>(b + pl.counters);
+  s.bucket_off = s.bucket_cnt = s.bucket_ent = nullptr;   // no room for the bucket index: probe hot_idx
   unsigned long long* nd = reinterpret_cast<unsigned long long*>(b + pl.n_out);
 
   int sms = 0;
