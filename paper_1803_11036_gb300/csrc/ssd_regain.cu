@@ -102,16 +102,30 @@ __device__ void build_buckets(const Dims& d, const Scratch& s, uint32_t i) {
   for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) ent[atomicAdd(&cnt[col[j] & d.low_mask], 1u)] = j;
 }
 
-constexpr int TA = 32, KW = 64;
+constexpr int TA = 64, KW = 64;
 
-// Blocks [0, pair_blocks) test the pairs; with the bucket index, block
-// pair_blocks + m builds the buckets of row 2 + m.
+// popcount(a) + popcount(b) through one carry-save step into `ones`: returns the
+// carries' popcount (weight 2) and leaves the sum bits in `ones`; the total of a
+// run is 2 * (sum of the returned counts) + popcount(ones).
+__device__ __forceinline__ uint32_t csa_pop(uint32_t& ones, uint32_t a, uint32_t b) {
+  const uint32_t carry = (ones & a) | (ones & b) | (a & b);
+  ones ^= a ^ b;
+  return __popc(carry);
+}
+
+// Blocks [0, pair_blocks) test the pairs in 64 x 64 tiles (4 x 4 per thread,
+// output columns interleaved by 16 so the shared-memory reads are free of bank
+// conflicts); with the bucket index, block pair_blocks + m builds the buckets of
+// row 2 + m.
 __global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s, uint32_t pair_blocks) {
   if (blockIdx.x >= pair_blocks) {
     build_buckets(d, s, 2 + (blockIdx.x - pair_blocks));
     return;
   }
   __shared__ uint32_t A[TA][KW + 1], B[TA][KW + 1];
+  __shared__ uint32_t wsum[kBlock / 32];
+  __shared__ unsigned long long tile_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t n0 = min(s.counters->hot[0], d.hse_cap);
   const uint32_t n1 = min(s.counters->hot[1], d.hse_cap);
   const uint64_t t1 = (n1 + TA - 1) / TA;
@@ -122,84 +136,193 @@ __global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s,
   const uint32_t* bm1 = s.pool_bm + (uint64_t)d.hse_cap * d.words;
   for (uint64_t t = blockIdx.x; t < ntiles; t += pair_blocks) {
     const uint32_t a0 = (uint32_t)(t / t1) * TA, b0 = (uint32_t)(t % t1) * TA;
-    uint32_t acc[2][2] = {{0, 0}, {0, 0}};
+    uint32_t ones[4][4], twice[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) ones[u][v] = twice[u][v] = 0;
     if (prune) {
       for (uint32_t k0 = 0; k0 < d.words; k0 += KW) {
         const uint32_t kw = d.words - k0 < (uint32_t)KW ? d.words - k0 : (uint32_t)KW;
         __syncthreads();
         for (int e = threadIdx.x; e < TA * KW; e += kBlock) {
           const int rr = e / KW, cc = e % KW;
-          const bool in = cc < (int)kw;
+          const bool in = cc < (int)kw;   // words past kw are staged as 0
           A[rr][cc] = (in && a0 + rr < n0) ? bm0[(uint64_t)(a0 + rr) * d.words + k0 + cc] : 0u;
           B[rr][cc] = (in && b0 + rr < n1) ? bm1[(uint64_t)(b0 + rr) * d.words + k0 + cc] : 0u;
         }
         __syncthreads();
-        for (uint32_t cc = 0; cc < kw; ++cc) {
-          const uint32_t x0 = A[2 * ty][cc], x1 = A[2 * ty + 1][cc];
-          const uint32_t y0 = B[2 * tx][cc], y1 = B[2 * tx + 1][cc];
-          acc[0][0] += __popc(x0 & y0);
-          acc[0][1] += __popc(x0 & y1);
-          acc[1][0] += __popc(x1 & y0);
-          acc[1][1] += __popc(x1 & y1);
+        for (uint32_t cc = 0; cc < kw; cc += 2) {
+          uint32_t x0[4], x1[4], y0[4], y1[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            x0[u] = A[ty + 16 * u][cc];
+            x1[u] = A[ty + 16 * u][cc + 1];
+            y0[u] = B[tx + 16 * u][cc];
+            y1[u] = B[tx + 16 * u][cc + 1];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) twice[u][v] += csa_pop(ones[u][v], x0[u] & y0[v], x1[u] & y1[v]);
+        }
+      }
+    }
+    // the tile's kept pairs go to the candidate buffer with one atomic per tile:
+    // a block-wide scan of the threads' counts gives each its offset
+    uint32_t keepm = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint32_t ia = a0 + ty + 16 * u, ib = b0 + tx + 16 * v;
+        const uint32_t rk = 2 * twice[u][v] + __popc(ones[u][v]);
+        if (ia < n0 && ib < n1 && (!prune || rk >= d.thr)) keepm |= 1u << (4 * u + v);
+      }
+    const uint32_t mine = __popc(keepm);
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t x = wsum[w];
+        wsum[w] = run;
+        run += x;
+      }
+      tile_base = run ? atomicAdd(&s.counters->level[1], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = tile_base + wsum[wid] + (incl - mine);
+    while (keepm) {
+      const int b = __ffs(keepm) - 1;
+      keepm &= keepm - 1;
+      const uint32_t ia = a0 + ty + 16 * (b >> 2), ib = b0 + tx + 16 * (b & 3);
+      if (pos < d.ctb_cap) {
+        s.ctb[0][pos * d.r + 0] = ia;
+        s.ctb[0][pos * d.r + 1] = ib;
+      } else {
+        atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
+      }
+      ++pos;
+    }
+    __syncthreads();   // wsum / tile_base are reused by the next tile
+  }
+}
+
+// Popcount of the AND of the "recorder < k" bitmaps of tuple tl (rows 0..i-1)
+// and row-i estimator idx over words [w0, w0 + n) (n a multiple of 4): all the
+// 16-byte loads of the share are issued before any is used.
+__device__ __forceinline__ uint32_t union_share(const Dims& d, const Scratch& s, uint32_t i,
+                                                const uint32_t (&tl)[SSD_MAX_R], uint32_t idx, uint32_t w0,
+                                                uint32_t n) {
+  const uint64_t cap = d.hse_cap;
+  const uint32_t* mine = s.pool_bm + ((uint64_t)i * cap + idx) * d.words + w0;
+  uint32_t sum = 0;
+  for (uint32_t w = 0; w < n; w += 16) {
+    uint4 x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = w + 4 * q < n ? *reinterpret_cast<const uint4*>(mine + w + 4 * q)
+                                                      : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (uint32_t j = 0; j < SSD_MAX_R; ++j) {
+      if (j < i) {
+        const uint32_t* row = s.pool_bm + ((uint64_t)j * cap + tl[j]) * d.words + w0 + w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (w + 4 * q < n) {
+            const uint4 y = *reinterpret_cast<const uint4*>(row + 4 * q);
+            x[q].x &= y.x; x[q].y &= y.y; x[q].z &= y.z; x[q].w &= y.w;
+          }
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        const uint32_t ia = a0 + 2 * ty + u, ib = b0 + 2 * tx + v;
-        const bool ok = ia < n0 && ib < n1 && (!prune || acc[u][v] >= d.thr);
-        const unsigned long long pos = warp_append(ok, &s.counters->level[1]);
-        if (ok) {
-          if (pos < d.ctb_cap) {
-            s.ctb[0][pos * d.r + 0] = ia;
-            s.ctb[0][pos * d.r + 1] = ib;
-          } else {
-            atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
-          }
-        }
-      }
+    for (int q = 0; q < 4; ++q) sum += __popc(x[q].x) + __popc(x[q].y) + __popc(x[q].z) + __popc(x[q].w);
   }
+  return sum;
 }
 
-// One candidate tuple c of row level i extended by row-i estimator idx (pool
-// index; kNone when this lane has none): the union test by the whole warp, then
-// the append to the next candidate buffer or, at the last row, the final test,
-// the host and its staging. Every lane of the warp makes the call.
-__device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* rctb,
-                                          uint32_t* sctb, uint64_t c, uint32_t idx, int lane) {
+// R_k of the union for every lane with a hit (idx != kNone; tl its candidate's
+// tuple), computed by the warp together. Every lane of the warp makes the call.
+// With bitmaps of a multiple of 16 words, groups of 4 lanes take up to 8 hits at
+// a time, each lane a quarter of the words; otherwise the whole warp takes the
+// hits one after another.
+__device__ __forceinline__ uint32_t union_rk(const Dims& d, const Scratch& s, uint32_t i,
+                                             const uint32_t (&tl)[SSD_MAX_R], uint32_t idx, int lane) {
+  const bool hit = idx != kNone;
+  unsigned m = __ballot_sync(kFull, hit);
+  uint32_t pc = 0;
+  if ((d.words & 15u) == 0) {
+    const int grp = lane >> 2;
+    const uint32_t per = d.words >> 2;
+    while (m) {
+      unsigned mm = m;   // this group's hit: the (grp+1)-th lowest set bit of m
+      for (int k = 0; k < grp; ++k) mm &= mm - 1;
+      const bool busy = mm != 0;
+      const int src = busy ? __ffs(mm) - 1 : lane;
+      uint32_t tg[SSD_MAX_R];
+#pragma unroll
+      for (uint32_t j = 0; j < SSD_MAX_R; ++j) tg[j] = __shfl_sync(kFull, tl[j], src);
+      const uint32_t ig = __shfl_sync(kFull, idx, src);
+      uint32_t part = busy ? union_share(d, s, i, tg, ig, (lane & 3) * per, per) : 0u;
+      part += __shfl_xor_sync(kFull, part, 1);
+      part += __shfl_xor_sync(kFull, part, 2);
+      const uint32_t rank = __popc(m & ((1u << lane) - 1u));
+      const uint32_t got = __shfl_sync(kFull, part, (rank < 8 ? rank : 0) * 4);
+      if (((m >> lane) & 1u) && rank < 8) pc = got;
+      for (int k = 0; k < 8 && m; ++k) m &= m - 1;
+    }
+    return pc;
+  }
+  const uint64_t cap = d.hse_cap;
+  while (m) {
+    const int L = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t idxL = __shfl_sync(kFull, idx, L);
+    uint32_t tL[SSD_MAX_R];
+#pragma unroll
+    for (uint32_t j = 0; j < SSD_MAX_R; ++j) tL[j] = __shfl_sync(kFull, tl[j], L);
+    uint32_t sum = 0;
+    for (uint32_t w = lane; w < d.words; w += 32) {
+      uint32_t x = s.pool_bm[((uint64_t)i * cap + idxL) * d.words + w];
+#pragma unroll
+      for (uint32_t j = 0; j < SSD_MAX_R; ++j)
+        if (j < i) x &= s.pool_bm[((uint64_t)j * cap + tL[j]) * d.words + w];
+      sum += __popc(x);
+    }
+    sum = __reduce_add_sync(kFull, sum);
+    if (lane == L) pc = sum;
+  }
+  return pc;
+}
+
+// One candidate tuple c (its pool indices tl, rows 0..i-1) of row level i
+// extended by row-i estimator idx (pool index; kNone when this lane has none):
+// the union test, then the append to the next candidate buffer or, at the last
+// row, the final test, the host and its staging. Every lane of the warp makes
+// the call (the test and the appends are warp-wide).
+__device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint32_t i, uint32_t* sctb,
+                                          const uint32_t (&tl)[SSD_MAX_R], uint32_t idx, int lane) {
   const uint64_t cap = d.hse_cap;
   const bool last = (i == d.r - 1);
   const bool prune = !(d.flags & SSD_NO_PRUNE);
   const bool verify = (d.flags & SSD_VERIFY_H0) != 0;
   const bool hit = idx != kNone;
-  uint32_t pc = 0;
-  if (prune || last) {
-    unsigned m = __ballot_sync(kFull, hit);
-    while (m) {
-      const int L = __ffs(m) - 1;
-      m &= m - 1;
-      const uint64_t cL = __shfl_sync(kFull, c, L);
-      const uint32_t idxL = __shfl_sync(kFull, idx, L);
-      const uint32_t* tL = rctb + cL * d.r;
-      uint32_t sum = 0;
-      for (uint32_t w = lane; w < d.words; w += 32) {
-        uint32_t x = s.pool_bm[((uint64_t)i * cap + idxL) * d.words + w];
-        for (uint32_t j = 0; j < i; ++j) x &= s.pool_bm[((uint64_t)j * cap + tL[j]) * d.words + w];
-        sum += __popc(x);
-      }
-      sum = __reduce_add_sync(kFull, sum);
-      if (lane == L) pc = sum;
-    }
-  }
+  const uint32_t pc = (prune || last) ? union_rk(d, s, i, tl, idx, lane) : 0u;
   const bool keep = hit && (!prune || pc >= d.thr);
   if (!last) {
     const unsigned long long pos = warp_append(keep, &s.counters->level[i]);
     if (keep) {
       if (pos < d.ctb_cap) {
-        const uint32_t* tup = rctb + c * d.r;
-        for (uint32_t j = 0; j < i; ++j) sctb[pos * d.r + j] = tup[j];
+#pragma unroll
+        for (uint32_t j = 0; j < SSD_MAX_R; ++j)
+          if (j < i) sctb[pos * d.r + j] = tl[j];
         sctb[pos * d.r + i] = idx;
       } else {
         atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
@@ -210,9 +333,10 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
     bool acc = hit && pc >= d.thr;
     uint32_t cip = 0;
     if (acc) {
-      const uint32_t* tup = rctb + c * d.r;
       uint32_t he[SSD_MAX_R];
-      for (uint32_t j = 0; j < i; ++j) he[j] = s.pool_col[(uint64_t)j * cap + tup[j]];
+#pragma unroll
+      for (uint32_t j = 0; j < SSD_MAX_R; ++j)
+        if (j < i) he[j] = s.pool_col[(uint64_t)j * cap + tl[j]];
       he[i] = s.pool_col[(uint64_t)i * cap + idx];
       acc = regain_host(d, he, &cip);
       if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
@@ -225,10 +349,18 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
   }
 }
 
-// The low q-delta bits the overlap test fixes for row i's estimator of candidate c.
-__device__ __forceinline__ uint32_t fixed_low(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* tup) {
-  const uint32_t he0 = s.pool_col[tup[0]];
-  const uint32_t hep = s.pool_col[(uint64_t)(i - 1) * d.hse_cap + tup[i - 1]];
+// Candidate c's tuple (rows 0..i-1) and the low q-delta bits the overlap test
+// fixes for its row-i estimator.
+__device__ __forceinline__ uint32_t load_candidate(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* tup,
+                                                   uint32_t (&tl)[SSD_MAX_R]) {
+#pragma unroll
+  for (uint32_t j = 0; j < SSD_MAX_R; ++j) tl[j] = j < i ? tup[j] : 0u;
+  const uint32_t he0 = s.pool_col[tl[0]];
+  uint32_t tp = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < SSD_MAX_R; ++j)
+    if (j == i - 1) tp = tl[j];
+  const uint32_t hep = s.pool_col[(uint64_t)(i - 1) * d.hse_cap + tp];
   const uint32_t want_low = (he0 ^ hep) >> d.delta;  // high q-delta bits of B(i-1)
   return (he0 ^ want_low) & d.low_mask;
 }
@@ -239,6 +371,9 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
   const unsigned long long avail = s.counters->level[i - 1];
   const uint64_t nc = avail < d.ctb_cap ? avail : d.ctb_cap;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t tl[SSD_MAX_R];   // the lane's candidate tuple (zero for a lane without one)
+#pragma unroll
+  for (uint32_t j = 0; j < SSD_MAX_R; ++j) tl[j] = 0;
   if (s.bucket_off) {
     // one candidate per lane; round p takes each lane's p-th bucket entry
     const uint32_t nb = 1u << d.low_bits;
@@ -248,12 +383,12 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
       const uint64_t c = w0 + lane;
       uint32_t b = 0, e = 0;
       if (c < nc) {
-        const uint32_t low = fixed_low(d, s, i, rctb + c * d.r);
+        const uint32_t low = load_candidate(d, s, i, rctb + c * d.r, tl);
         b = off[low];
         e = off[low + 1];
       }
       for (uint32_t p = 0; __any_sync(kFull, b + p < e); ++p)
-        level_hit(d, s, i, rctb, sctb, c, b + p < e ? ent[b + p] : kNone, lane);
+        level_hit(d, s, i, sctb, tl, b + p < e ? ent[b + p] : kNone, lane);
     }
     return;
   }
@@ -261,14 +396,13 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
   const uint64_t total = nc << d.delta;
   for (uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < total; w0 += stride) {
     const uint64_t item = w0 + lane;
-    const uint64_t c = item >> d.delta;
     uint32_t idx = kNone;
     if (item < total) {
       const uint32_t h = (uint32_t)(item & ((1u << d.delta) - 1u));
-      const uint32_t he_i = (h << d.low_bits) | fixed_low(d, s, i, rctb + c * d.r);
+      const uint32_t he_i = (h << d.low_bits) | load_candidate(d, s, i, rctb + (item >> d.delta) * d.r, tl);
       idx = s.hot_idx[((uint64_t)i << d.q) | he_i];
     }
-    level_hit(d, s, i, rctb, sctb, c, idx, lane);
+    level_hit(d, s, i, sctb, tl, idx, lane);
   }
 }
 
