@@ -139,6 +139,29 @@ SSD_API int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot);
 /* Set the slot counter (host bookkeeping only, no GPU work): after replaying a
  * captured slot the caller advances the counters the replay cannot. */
 SSD_API int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot);
+/* What a sketch counts (its view). Sec. 3.1 defines sliding super points for
+ * the hosts of CNet, the first field of each pair, and obtains those of ONet by
+ * exchanging the roles of the two networks; Sec. 6 scales to bigger networks by
+ * keeping several RSEAs, each regaining one group of hosts split by their IP
+ * addresses.
+ *   side: SSD_SIDE_CNET - hosts are the first field of a pair, opposite hosts
+ *         the second (the default); SSD_SIDE_ONET - the other way round;
+ *   group_bits (0..SSD_MAX_GROUP_BITS), group (< 2^group_bits): the sketch takes
+ *         only pairs whose host has `group` as its top group_bits bits; every
+ *         scan skips the others, and a regain of the sketch lists only hosts of
+ *         the group (a tuple naming a host of another group is rejected: no pair
+ *         of that host reached the sketch). group_bits = 0: every host.
+ * A view is set before the sketch's first scan (SSD_ESTATE once it has advanced
+ * a slot; scans made earlier in slot 0 counted under the old view). Calls that
+ * combine sketches (ssd_merge, ssd_close_slot, ssd_slot) need one view for all
+ * of them (SSD_EINVAL) and the global sketch takes it; ssd_scan_batch may mix
+ * views, so one launch can scan the same pairs for both sides (bidirectional
+ * detection) or for every group. */
+#define SSD_SIDE_CNET 0u
+#define SSD_SIDE_ONET 1u
+#define SSD_MAX_GROUP_BITS 16
+SSD_API int ssd_sketch_set_view(ssd_sketch* s, uint32_t side, uint32_t group_bits, uint32_t group);
+SSD_API int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group_bits, uint32_t* group);
 /* Copy `count` recorders starting at recorder `first` to dst (host or device).
  * Waits for `stream` before returning. Checkpointing a sketch is
  * export + ssd_sketch_slot; resuming is import. */

@@ -217,6 +217,28 @@ def regain(p: Params, tables: np.ndarray, sk: np.ndarray, method: str = "levelwi
     return dict(ips=ips[:n].copy(), rk=rks[:n].copy(), levels=levels[: p.r].copy(), raw=rawv)
 
 
+def view_pairs(pairs: np.ndarray, side: int = 0, group_bits: int = 0, group: int = 0) -> np.ndarray:
+    """The (host, opposite host) pairs one sketch view counts. Sec. 3.1 defines the detector for
+    the hosts of CNet, the first field of each pair, and obtains ONet's by exchanging the roles of
+    the two networks (side 1 swaps the fields). Sec. 6 scales to bigger networks with several RSEAs,
+    each regaining one group of hosts split by their IP addresses: a group keeps the pairs whose
+    host has `group` as its top group_bits bits."""
+    a = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    if side:
+        a = a[:, ::-1]
+    if group_bits:
+        a = a[(a[:, 0] >> np.uint32(32 - group_bits)) == np.uint32(group)]
+    return np.ascontiguousarray(a)
+
+
+def in_group(ips: np.ndarray, group_bits: int, group: int) -> np.ndarray:
+    """Mask of the hosts of one IP group (Sec. 6): the regain of a group's RSEA lists only these."""
+    ips = np.asarray(ips, dtype=np.uint32)
+    if not group_bits:
+        return np.ones(ips.shape, dtype=bool)
+    return (ips >> np.uint32(32 - group_bits)) == np.uint32(group)
+
+
 class Sampled:
     """Algorithm 2 and the recorder update restricted to chosen estimators (row, col)."""
 

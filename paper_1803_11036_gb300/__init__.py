@@ -22,7 +22,8 @@ import weakref
 
 import numpy as np
 
-from ._abi import (SSD_ECAPACITY, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SLOT_CHUNKED,  # noqa: F401
+from ._abi import (SSD_ECAPACITY, SSD_MAX_GROUP_BITS, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SIDE_CNET,  # noqa: F401
+                   SSD_SIDE_ONET, SSD_SLOT_CHUNKED,
                    SSD_STATUS_CTB_OVERFLOW,
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
                    TUNING_FIELDS, Params, SSDError, Stats, Tuning, check, load)
@@ -100,6 +101,20 @@ class Sketch:
     @slot.setter
     def slot(self, value: int) -> None:
         check(self.ctx.L.ssd_sketch_set_slot(self._h, value), "ssd_sketch_set_slot")
+
+    @property
+    def view(self) -> tuple[int, int, int]:
+        """(side, group_bits, group): which hosts the sketch counts (see ssd_sketch_set_view)."""
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        check(self.ctx.L.ssd_sketch_view(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+              "ssd_sketch_view")
+        return a.value, b.value, c.value
+
+    def set_view(self, side: int = SSD_SIDE_CNET, group_bits: int = 0, group: int = 0) -> "Sketch":
+        """Count the hosts of `side` (SSD_SIDE_CNET: first field of a pair; SSD_SIDE_ONET: second)
+        whose top group_bits bits are `group`. Before the sketch's first scan."""
+        check(self.ctx.L.ssd_sketch_set_view(self._h, side, group_bits, group), "ssd_sketch_set_view")
+        return self
 
     def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
         """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""

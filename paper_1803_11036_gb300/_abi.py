@@ -17,6 +17,8 @@ SSD_NO_PRUNE = 2
 SSD_SLOT_CHUNKED = 4
 SSD_MAX_R = 8
 SSD_MAX_ROUTERS = 128
+SSD_SIDE_CNET, SSD_SIDE_ONET = 0, 1
+SSD_MAX_GROUP_BITS = 16
 SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_CTB_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_STATUS_LIST_OVERFLOW = 1, 2, 4, 8
 
 
@@ -58,6 +60,8 @@ SIGNATURES = {
     "ssd_sketch_bytes": ([_vp], _u64),
     "ssd_sketch_slot": ([_vp, ctypes.POINTER(_u64)], _int),
     "ssd_sketch_set_slot": ([_vp, _u64], _int),
+    "ssd_sketch_set_view": ([_vp, _u32, _u32, _u32], _int),
+    "ssd_sketch_view": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _int),
     "ssd_sketch_export": ([_vp, _u64, _u64, _vp, _vp], _int),
     "ssd_sketch_import": ([_vp, _vp, _u64, _vp], _int),
     "ssd_scan": ([_vp, _vp, _u64, _vp], _int),

@@ -54,6 +54,7 @@ struct ssd_sketch {
   int device;
   uint16_t* dr;
   uint64_t slot;
+  uint32_t view;   // ssd::view_pack(side, group bits, group)
 };
 
 namespace {
@@ -111,7 +112,16 @@ bool same_ctx(ssd_sketch* const* v, int n, ssd_ctx** ctx) {
   return true;
 }
 
-int add_job(ssd::ScanBatch& b, int j, uint16_t* dr, const uint32_t* pairs, uint64_t n, uint64_t* prefix) {
+// Sketches that are combined (merged) must count the same hosts.
+bool same_view(ssd_sketch* const* v, int n) {
+  for (int i = 1; i < n; ++i)
+    if (v[i]->view != v[0]->view) return false;
+  return true;
+}
+
+int add_job(ssd::ScanBatch& b, int j, const ssd_sketch* sk, const uint32_t* pairs, uint64_t n, uint64_t* prefix) {
+  uint16_t* dr = sk->dr;
+  b.view[j] = sk->view;
   if (n && !pairs) return SSD_EINVAL;
   if (reinterpret_cast<uintptr_t>(pairs) & 7u) return SSD_EINVAL;
   const uint32_t* head = nullptr;
@@ -168,9 +178,9 @@ int trace(ssd_ctx* ctx, cudaEvent_t ev, cudaStream_t st) {
 }
 
 int regain_after_pass(ssd_ctx* ctx, uint32_t* ips, uint32_t* rk, uint64_t cap, unsigned long long* n_out,
-                      cudaStream_t st) {
+                      cudaStream_t st, uint32_t view) {
   int launches = 0;
-  cudaError_t e = ssd::launch_regain_tail(ctx->d, ctx->s, ips, rk, cap, n_out, ctx->sms, st, &launches);
+  cudaError_t e = ssd::launch_regain_tail(ctx->d, ctx->s, ips, rk, cap, n_out, ctx->sms, st, &launches, view);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(e, "regain kernels");
   return SSD_OK;
@@ -221,7 +231,7 @@ void free_ctx(ssd_ctx* c) {
 
 extern "C" {
 
-int ssd_version(void) { return 101; }
+int ssd_version(void) { return 102; }
 
 const char* ssd_strerror(int code) {
   switch (code) {
@@ -362,6 +372,7 @@ int ssd_sketch_create(ssd_ctx* ctx, ssd_sketch** out) {
   s->ctx = ctx;
   s->device = ctx->device;
   s->slot = 0;
+  s->view = 0;
   s->dr = nullptr;
   const uint64_t bytes = ssd_sketch_bytes(ctx);
   if (cudaMalloc(&s->dr, bytes) != cudaSuccess) {
@@ -400,6 +411,22 @@ int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot) {
   return SSD_OK;
 }
 
+int ssd_sketch_set_view(ssd_sketch* s, uint32_t side, uint32_t group_bits, uint32_t group) {
+  if (!s || side > SSD_SIDE_ONET || group_bits > SSD_MAX_GROUP_BITS) return SSD_EINVAL;
+  if (group >> group_bits) return SSD_EINVAL;
+  if (s->slot != 0) return SSD_ESTATE;
+  s->view = ssd::view_pack(side, group_bits, group);
+  return SSD_OK;
+}
+
+int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group_bits, uint32_t* group) {
+  if (!s || !side || !group_bits || !group) return SSD_EINVAL;
+  *side = s->view & 1u;
+  *group_bits = (s->view >> 1) & 31u;
+  *group = s->view >> 16;
+  return SSD_OK;
+}
+
 int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
   if (!s || (count && !dst)) return SSD_EINVAL;
   const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;
@@ -435,7 +462,7 @@ int ssd_scan_batch(ssd_sketch* const* sketches, const uint32_t* const* d_pairs, 
   uint64_t prefix = 0;
   bool any_edge = false;
   for (int j = 0; j < n; ++j) {
-    int rc = add_job(b, j, sketches[j]->dr, d_pairs[j], n_pairs[j], &prefix);
+    int rc = add_job(b, j, sketches[j], d_pairs[j], n_pairs[j], &prefix);
     if (rc != SSD_OK) return rc;
     any_edge = any_edge || b.edge[2 * j] || b.edge[2 * j + 1];
   }
@@ -505,6 +532,7 @@ int ssd_advance(ssd_sketch* const* sketches, int n, void* stream) {
 int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, void* stream) {
   ssd_ctx* ctx = nullptr;
   if (!same_ctx(routers, n, &ctx) || !global || global->ctx != ctx) return SSD_EINVAL;
+  if (!same_view(routers, n)) return SSD_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (routers[i] == global) return SSD_EINVAL;
     if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
@@ -513,6 +541,7 @@ int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, void* strea
   int rc = stream_pass(ctx, routers, n, global->dr, 0, as_stream(stream));
   if (rc != SSD_OK) return rc;
   global->slot = routers[0]->slot;
+  global->view = routers[0]->view;
   return SSD_OK;
 }
 
@@ -527,7 +556,7 @@ int ssd_regain(ssd_ctx* ctx, const ssd_sketch* global, uint32_t* d_ips, uint32_t
   ssd_sketch* one = const_cast<ssd_sketch*>(global);
   rc = stream_pass(ctx, &one, 1, nullptr, ssd::kHot, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_pass, st);
-  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, ctx->n_out, st);
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, ctx->n_out, st, global->view);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   ssd::DevCounters h;
@@ -546,6 +575,7 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx) return SSD_EINVAL;
   if (global && global->ctx != ctx) return SSD_EINVAL;
   if (cap && (!d_ips || !d_rk)) return SSD_EINVAL;
+  if (!same_view(routers, n)) return SSD_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (routers[i] == global) return SSD_EINVAL;
     if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
@@ -558,12 +588,15 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   rc = stream_pass(ctx, routers, n, global ? global->dr : nullptr, ssd::kAdvance | ssd::kHot, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
-  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, routers[0]->view);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   const uint64_t merged = routers[0]->slot;
   for (int i = 0; i < n; ++i) routers[i]->slot += 1;
-  if (global) global->slot = merged;
+  if (global) {
+    global->slot = merged;
+    global->view = routers[0]->view;
+  }
   return SSD_OK;
 }
 
@@ -579,14 +612,15 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   std::memset(&b, 0, sizeof(b));
   b.n = 1;
   uint64_t nvec = 0;
-  int rc = add_job(b, 0, router->dr, pairs, n_pairs, &nvec);
+  int rc = add_job(b, 0, router, pairs, n_pairs, &nvec);
   if (rc != SSD_OK) return rc;
   b.prefix[1] = nvec;
   const uint64_t tgrid = scan_grid(ctx, nvec);
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
-  // both hashes of every pair once per slot when they pack into one word
-  const bool prehash = d.q + d.log2_eta <= 32;
+  // both hashes of every pair once per slot when they pack into one word (a grouped view
+  // keeps the raw pairs: a pair outside the group must be skippable)
+  const bool prehash = d.q + d.log2_eta <= 32 && ((router->view >> 1) & 31u) == 0;
   if (prehash && n_pairs > ctx->packed_cap) {  // a larger slot than any before: grow (waits for `stream`)
     SSD_CUDA(cudaStreamSynchronize(st));
     cudaFree(ctx->packed);
@@ -607,6 +641,7 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   std::memset(&a, 0, sizeof(a));
   a.router = router->dr;
   a.global = global ? global->dr : nullptr;
+  a.view = router->view;
   cudaError_t e;
   if (prehash) {
     if (n_pairs) {
@@ -648,10 +683,13 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   }
   rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
-  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, router->view);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
-  if (global) global->slot = router->slot;
+  if (global) {
+    global->slot = router->slot;
+    global->view = router->view;
+  }
   router->slot += 1;
   return SSD_OK;
 }
@@ -663,6 +701,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   if (!ctx || !same_ctx(routers, n, &c2) || c2 != ctx || !d_pairs || !n_pairs) return SSD_EINVAL;
   if (global && global->ctx != ctx) return SSD_EINVAL;
   if (cap && (!d_ips || !d_rk)) return SSD_EINVAL;
+  if (!same_view(routers, n)) return SSD_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (routers[i] == global) return SSD_EINVAL;
     if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
@@ -689,7 +728,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   b.n = n;
   uint64_t prefix = 0;
   for (int j = 0; j < n; ++j) {
-    int rc = add_job(b, j, routers[j]->dr, d_pairs[j], n_pairs[j], &prefix);
+    int rc = add_job(b, j, routers[j], d_pairs[j], n_pairs[j], &prefix);
     if (rc != SSD_OK) return rc;
   }
   b.prefix[n] = prefix;
@@ -727,12 +766,15 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   }
   rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
-  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st);
+  if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, routers[0]->view);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   const uint64_t merged = routers[0]->slot;
   for (int i = 0; i < n; ++i) routers[i]->slot += 1;
-  if (global) global->slot = merged;
+  if (global) {
+    global->slot = merged;
+    global->view = routers[0]->view;
+  }
   return SSD_OK;
 }
 

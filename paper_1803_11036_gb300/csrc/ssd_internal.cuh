@@ -81,7 +81,26 @@ struct ScanBatch {
   uint16_t* dr[kMaxBatch];
   const uint4* vec[kMaxBatch];
   const uint32_t* edge[2 * kMaxBatch];  // head, tail per router (nullptr when absent)
+  uint32_t view[kMaxBatch];             // each job's sketch view (view_pair)
 };
+
+// A sketch's view, packed: bit 0 = side (1: hosts are the second field of a
+// pair), bits 1..5 = group bits gb, bits 16..31 = group. With gb > 0 only hosts
+// whose top gb bits equal the group are counted.
+__host__ __device__ __forceinline__ uint32_t view_pack(uint32_t side, uint32_t gb, uint32_t group) {
+  return (side & 1u) | (gb << 1) | (group << 16);
+}
+__host__ __device__ __forceinline__ bool view_host_in(uint32_t view, uint32_t host) {
+  const uint32_t gb = (view >> 1) & 31u;
+  return gb == 0 || (host >> (32u - gb)) == (view >> 16);
+}
+// The (host, opposite host) a view takes from the stored pair (x, y); false when
+// the host is outside the view's group.
+__device__ __forceinline__ bool view_pair(uint32_t view, uint32_t x, uint32_t y, uint32_t& cip, uint32_t& oip) {
+  cip = (view & 1u) ? y : x;
+  oip = (view & 1u) ? x : y;
+  return view_host_in(view, cip);
+}
 cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& b, int grid, const Tuning& tn,
                         cudaStream_t st);
 
@@ -190,7 +209,8 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
 
 // ---- per-slot pre-hash of one router's pairs (ssd_scan.cu) ----
 // out[m] = (cip, RHFG[0](cip) | H1(oip) << q) for every pair of the buffer described by
-// job 0 of b: the body vectors first (out[2v], out[2v+1]), then the head and tail pairs.
+// job 0 of b, taken through job 0's view (its side; a grouped view is not pre-hashed):
+// the body vectors first (out[2v], out[2v+1]), then the head and tail pairs.
 // The result holds n_pairs entries in an order the order-free scan does not see.
 cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint2* out, int grid,
                            cudaStream_t st);
@@ -214,13 +234,16 @@ struct ChunkArgs {
   uint64_t nvec;
   const uint32_t* edge[2];   // head / tail pair outside the body, or nullptr
   int packed;                // vec/edge[0] hold pre-hashed pairs (edge[1] unused)
+  uint32_t view;             // the router's view (raw pairs; pre-hashed pairs are already in it)
 };
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st);
 
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.
+// `view`: the regained sketch's view; hosts outside its group are not listed.
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
-                               unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches);
+                               unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches,
+                               uint32_t view = 0);
 
 }  // namespace ssd

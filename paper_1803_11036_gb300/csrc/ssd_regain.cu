@@ -308,7 +308,7 @@ __device__ __forceinline__ uint32_t union_rk(const Dims& d, const Scratch& s, ui
 // row, the final test, the host and its staging. Every lane of the warp makes
 // the call (the test and the appends are warp-wide).
 __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint32_t i, uint32_t* sctb,
-                                          const uint32_t (&tl)[SSD_MAX_R], uint32_t idx, int lane) {
+                                          const uint32_t (&tl)[SSD_MAX_R], uint32_t idx, int lane, uint32_t view) {
   const uint64_t cap = d.hse_cap;
   const bool last = (i == d.r - 1);
   const bool prune = !(d.flags & SSD_NO_PRUNE);
@@ -340,6 +340,7 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
       he[i] = s.pool_col[(uint64_t)i * cap + idx];
       acc = regain_host(d, he, &cip);
       if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
+      if (acc) acc = view_host_in(view, cip);   // a grouped sketch holds only its group's hosts
     }
     const unsigned long long pos = warp_append(acc, &s.counters->raw);
     if (acc) {
@@ -366,7 +367,8 @@ __device__ __forceinline__ uint32_t load_candidate(const Dims& d, const Scratch&
 }
 
 __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s, const uint32_t i,
-                                                  const uint32_t* __restrict__ rctb, uint32_t* __restrict__ sctb) {
+                                                  const uint32_t* __restrict__ rctb, uint32_t* __restrict__ sctb,
+                                                  const uint32_t view) {
   const int lane = threadIdx.x & 31;
   const unsigned long long avail = s.counters->level[i - 1];
   const uint64_t nc = avail < d.ctb_cap ? avail : d.ctb_cap;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
         e = off[low + 1];
       }
       for (uint32_t p = 0; __any_sync(kFull, b + p < e); ++p)
-        level_hit(d, s, i, sctb, tl, b + p < e ? ent[b + p] : kNone, lane);
+        level_hit(d, s, i, sctb, tl, b + p < e ? ent[b + p] : kNone, lane, view);
     }
     return;
   }
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
       const uint32_t he_i = (h << d.low_bits) | load_candidate(d, s, i, rctb + (item >> d.delta) * d.r, tl);
       idx = s.hot_idx[((uint64_t)i << d.q) | he_i];
     }
-    level_hit(d, s, i, sctb, tl, idx, lane);
+    level_hit(d, s, i, sctb, tl, idx, lane, view);
   }
 }
 
@@ -488,7 +490,8 @@ __global__ void __launch_bounds__(kListThreads) k_list(const Dims d, const Scrat
 }  // namespace
 
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
-                               unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches) {
+                               unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches,
+                               uint32_t view) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -512,7 +515,7 @@ cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, u
     // level 1 (pairs) wrote ctb[0]; level i reads ctb[i & 1] and writes ctb[(i + 1) & 1]
     const uint32_t* rctb = s.ctb[i & 1];
     uint32_t* sctb = s.ctb[(i + 1) & 1];
-    k_level<<<sms * 8, kBlock, 0, st>>>(d, s, i, rctb, sctb);
+    k_level<<<sms * 8, kBlock, 0, st>>>(d, s, i, rctb, sctb, view);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches += 1;

@@ -28,6 +28,24 @@ __device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t ci
   }
 }
 
+// scan_pair on the stored pair (x, y) through a job's view (side and group).
+__device__ __forceinline__ void scan_view(uint16_t* __restrict__ dr, uint32_t view, uint32_t x, uint32_t y,
+                                          const uint32_t* sT, const Dims& d) {
+  uint32_t cip, oip;
+  if (view_pair(view, x, y, cip, oip)) scan_pair(dr, cip, oip, sT, d);
+}
+
+// touch_pair on the stored pair (x, y) through a job's view; every lane makes the
+// call (a pair outside the view's group takes part as a no-op).
+template <int CM>
+__device__ __forceinline__ void touch_view(uint32_t* bits, uint64_t jbase, uint32_t view, uint32_t x, uint32_t y,
+                                           bool live, const uint32_t* sT, const Dims& d, uint32_t r0, uint32_t r1,
+                                           uint64_t se0, uint64_t count) {
+  uint32_t cip, oip;
+  const bool in = view_pair(view, x, y, cip, oip);
+  touch_pair<CM>(bits, jbase, cip, oip, live && in, sT, d, r0, r1, se0, count);
+}
+
 __device__ __forceinline__ int find_router(const ScanBatch& b, uint64_t v) {
   int lo = 0, hi = b.n - 1;
   while (lo < hi) {  // last j with prefix[j] <= v
@@ -49,7 +67,7 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
   // 8 mod 16, a tail when the body leaves one packet over
   if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
     const uint32_t* e = b.edge[threadIdx.x];
-    if (e) scan_pair(b.dr[threadIdx.x >> 1], e[0], e[1], sT, d);
+    if (e) scan_view(b.dr[threadIdx.x >> 1], b.view[threadIdx.x >> 1], e[0], e[1], sT, d);
   }
 
   const uint64_t total = b.prefix[b.n];
@@ -58,43 +76,46 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
   if (b.n == 1) {
     const uint4* __restrict__ vec = b.vec[0];
     uint16_t* __restrict__ dr = b.dr[0];
+    const uint32_t view = b.view[0];
     for (; v + (U - 1) * stride < total; v += U * stride) {
       uint4 w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) w[u] = __ldcs(vec + v + u * stride);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        scan_pair(dr, w[u].x, w[u].y, sT, d);
-        scan_pair(dr, w[u].z, w[u].w, sT, d);
+        scan_view(dr, view, w[u].x, w[u].y, sT, d);
+        scan_view(dr, view, w[u].z, w[u].w, sT, d);
       }
     }
     for (; v < total; v += stride) {
       const uint4 w = __ldcs(vec + v);
-      scan_pair(dr, w.x, w.y, sT, d);
-      scan_pair(dr, w.z, w.w, sT, d);
+      scan_view(dr, view, w.x, w.y, sT, d);
+      scan_view(dr, view, w.z, w.w, sT, d);
     }
   } else {
     for (; v + (U - 1) * stride < total; v += U * stride) {
       uint4 w[U];
       uint16_t* dr[U];
+      uint32_t vw[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint64_t vv = v + u * stride;
         const int j = find_router(b, vv);
         w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
         dr[u] = b.dr[j];
+        vw[u] = b.view[j];
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        scan_pair(dr[u], w[u].x, w[u].y, sT, d);
-        scan_pair(dr[u], w[u].z, w[u].w, sT, d);
+        scan_view(dr[u], vw[u], w[u].x, w[u].y, sT, d);
+        scan_view(dr[u], vw[u], w[u].z, w[u].w, sT, d);
       }
     }
     for (; v < total; v += stride) {
       const int j = find_router(b, v);
       const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
-      scan_pair(b.dr[j], w.x, w.y, sT, d);
-      scan_pair(b.dr[j], w.z, w.w, sT, d);
+      scan_view(b.dr[j], b.view[j], w.x, w.y, sT, d);
+      scan_view(b.dr[j], b.view[j], w.z, w.w, sT, d);
     }
   }
 }
@@ -114,7 +135,9 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
   const uint32_t lane = threadIdx.x & 31u;
   if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
     const uint32_t* e = b.edge[threadIdx.x];
-    if (e) touch_pair<0>(bits, (uint64_t)(threadIdx.x >> 1) * count, e[0], e[1], true, sT, d, r0, r1, se0, count);
+    if (e)
+      touch_view<0>(bits, (uint64_t)(threadIdx.x >> 1) * count, b.view[threadIdx.x >> 1], e[0], e[1], true, sT, d, r0,
+                    r1, se0, count);
   }
   const uint64_t total = b.prefix[b.n];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -122,17 +145,19 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
   for (; vb + 31 + (U - 1) * stride < total; vb += U * stride) {
     uint4 w[U];
     uint64_t jb[U];
+    uint32_t vw[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint64_t vv = vb + lane + u * stride;
       const int j = b.n == 1 ? 0 : find_router(b, vv);
       w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
       jb[u] = (uint64_t)j * count;
+      vw[u] = b.view[j];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      touch_pair<CM>(bits, jb[u], w[u].x, w[u].y, true, sT, d, r0, r1, se0, count);
-      touch_pair<CM>(bits, jb[u], w[u].z, w[u].w, true, sT, d, r0, r1, se0, count);
+      touch_view<CM>(bits, jb[u], vw[u], w[u].x, w[u].y, true, sT, d, r0, r1, se0, count);
+      touch_view<CM>(bits, jb[u], vw[u], w[u].z, w[u].w, true, sT, d, r0, r1, se0, count);
     }
   }
   for (; vb < total; vb += stride) {
@@ -140,13 +165,15 @@ __global__ void __launch_bounds__(kBlock) k_touch(const Dims d, const uint32_t* 
     const bool live = v < total;
     uint4 w = make_uint4(0, 0, 0, 0);
     uint64_t jb = 0;
+    uint32_t vw = 0;
     if (live) {
       const int j = b.n == 1 ? 0 : find_router(b, v);
       w = __ldcs(b.vec[j] + (v - b.prefix[j]));
       jb = (uint64_t)j * count;
+      vw = b.view[j];
     }
-    touch_pair<CM>(bits, jb, w.x, w.y, live, sT, d, r0, r1, se0, count);
-    touch_pair<CM>(bits, jb, w.z, w.w, live, sT, d, r0, r1, se0, count);
+    touch_view<CM>(bits, jb, vw, w.x, w.y, live, sT, d, r0, r1, se0, count);
+    touch_view<CM>(bits, jb, vw, w.z, w.w, live, sT, d, r0, r1, se0, count);
   }
 }
 
@@ -157,7 +184,10 @@ __global__ void __launch_bounds__(kBlock) k_prehash(const Dims d, const uint32_t
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
   __syncthreads();
   const uint64_t nvec = b.prefix[1];
-  auto pack = [&](uint32_t cip, uint32_t oip) {
+  const uint32_t view = b.view[0];
+  auto pack = [&](uint32_t x, uint32_t y) {
+    uint32_t cip, oip;
+    view_pair(view, x, y, cip, oip);   // the side only: grouped views are not pre-hashed
     return make_uint2(cip, (tab_hash(sT + 1024, cip) & d.col_mask) | ((tab_hash(sT, oip) & (d.eta - 1u)) << d.q));
   };
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;

@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
       touch_packed<CM>(a.next, w.x, w.y, live, d, nr0, nr1, a.nx_se0, a.nx_count);
       touch_packed<CM>(a.next, w.z, w.w, live, d, nr0, nr1, a.nx_se0, a.nx_count);
     } else {
-      touch_pair<CM>(a.next, 0, w.x, w.y, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
-      touch_pair<CM>(a.next, 0, w.z, w.w, live, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      uint32_t c0, o0, c1, o1;
+      const bool in0 = view_pair(a.view, w.x, w.y, c0, o0), in1 = view_pair(a.view, w.z, w.w, c1, o1);
+      touch_pair<CM>(a.next, 0, c0, o0, live && in0, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+      touch_pair<CM>(a.next, 0, c1, o1, live && in1, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
   };
   for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
@@ -295,8 +297,13 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
       }
       if (e == 0 && lane < 2 && a.edge[lane]) {
         const uint32_t* p = a.edge[lane];
-        if (PACKED) touch_packed<0>(a.next, p[0], p[1], true, d, nr0, nr1, a.nx_se0, a.nx_count);
-        else touch_pair<0>(a.next, 0, p[0], p[1], true, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        if (PACKED) {
+          touch_packed<0>(a.next, p[0], p[1], true, d, nr0, nr1, a.nx_se0, a.nx_count);
+        } else {
+          uint32_t c0, o0;
+          const bool in = view_pair(a.view, p[0], p[1], c0, o0);
+          touch_pair<0>(a.next, 0, c0, o0, in, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
+        }
       }
     }
     pool_if_hot(d, s, se, cnt, my, lane);

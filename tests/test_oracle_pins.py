@@ -453,3 +453,27 @@ def test_precise_counter_bruteforce():
         assert list(zip(ips.tolist(), deg.tolist())) == expect
         for a, c in counts.items():
             assert ex.degree(a) == c
+
+
+def test_views_swap_and_partition():
+    """Sec. 3.1 / Sec. 6 views: the ONet view of a swapped stream is the CNet view of the original,
+    sketch for sketch; the groups of one group_bits split the pairs into disjoint parts that
+    together hold every pair, and each part holds only its group's hosts."""
+    W = tg.workload("tiny")
+    p = oracle.params(W["params"])
+    tabs = tg.hash_tables(W["hash_seed"])
+    pairs = tg.traffic_for(W).slot(0)[0]
+    swapped = np.ascontiguousarray(pairs[:, ::-1])
+    a, b = oracle.new_sketch(p), oracle.new_sketch(p)
+    oracle.scan(p, tabs, a, oracle.view_pairs(pairs))
+    oracle.scan(p, tabs, b, oracle.view_pairs(swapped, side=1))
+    assert np.array_equal(a, b)
+    assert np.array_equal(oracle.view_pairs(pairs), pairs)
+    for gb in (1, 3):
+        parts = [oracle.view_pairs(pairs, 0, gb, g) for g in range(1 << gb)]
+        assert sum(len(x) for x in parts) == len(pairs)
+        for g, part in enumerate(parts):
+            assert oracle.in_group(part[:, 0], gb, g).all()
+        both = np.concatenate(parts)
+        key = lambda a_: a_[:, 0].astype(np.uint64) << np.uint64(32) | a_[:, 1]
+        assert np.array_equal(np.sort(key(both)), np.sort(key(pairs)))
