@@ -62,6 +62,14 @@ extern "C" {
 /* ssd_slot, one router: collect every chunk's touch bits on the side stream, as
  * for several routers, instead of inside the streaming kernel. Same result. */
 #define SSD_SLOT_CHUNKED 4u
+/* Eq. 2 as printed: RHFG[i](cip) = ((cip >> (i*delta)) XOR RHFG[0](cip)) mod 2^q.
+ * By default the shift is (i-1)*delta, the only shift under which the stated
+ * condition (r-2)*delta + q >= 32 puts every bit of cip in some window B(i)
+ * (Eq. 3). With the printed shift no window holds bits 0..delta-1: a tuple
+ * fixes bits delta..31 only, and the regain tries the 2^delta completions and
+ * lists those whose RHFG[0] is he_0 (so the check of SSD_VERIFY_H0 is implied).
+ * For comparing the two readings. */
+#define SSD_RHFG_LITERAL 8u
 
 #define SSD_MAX_R 8
 #define SSD_MAX_ROUTERS 128
@@ -72,7 +80,7 @@ extern "C" {
  *       3 <= r <= SSD_MAX_R, 0 < delta < q <= 24, (r-2)*delta + q >= 32 (Eq. 2-3)
  *   k: window length in slots, 1 <= k <= 65534 (Sec. 3.2)
  *   theta: super point threshold (Def. 2), >= 1
- *   flags: SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED
+ *   flags: SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED | SSD_RHFG_LITERAL
  *   hse_capacity: hot estimators kept per row (0 = min(2^q, 65536))
  *   ctb_capacity: tuples per candidate tuple buffer (0 = 2^22)
  *   out_capacity: accepted tuples staged before the list is sorted (0 = 2^20)

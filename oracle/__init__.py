@@ -26,6 +26,7 @@ _lib = None
 
 VERIFY_H0 = 1
 MAX_MERGE = 2
+RHFG_LITERAL = 4   # Eq. 2 as printed: windows at i*delta (R2 takes (i-1)*delta)
 MAX_R = 16
 
 

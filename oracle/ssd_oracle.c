@@ -24,7 +24,10 @@
  *      Algorithm 1's literal MAX. ORC_MAX_MERGE selects the literal max merge.
  *   R2 Eq. 2 shifts by (i-1)*delta for i >= 1, the only shift for which the
  *      stated coverage condition (r-2)*delta+q >= 32 makes every bit of cip
- *      appear in some B(i).
+ *      appear in some B(i). ORC_RHFG_LITERAL takes Eq. 2 as printed, a shift of
+ *      i*delta: no window holds bits 0..delta-1, so a tuple fixes only bits
+ *      delta..31 and the regain tries the 2^delta completions, keeping those
+ *      whose RHFG[0] is he_0 (the only data that pins the missing bits).
  *   R3 the overlap test on adding row i compares the high q-delta bits of
  *      B(i-1) with the low q-delta bits of B(i), B(j) = he_0 XOR he_j.
  *   R4 a tuple is finished when it holds r estimators (rows 0..r-1).
@@ -46,6 +49,7 @@
 #define ORC_MAX_R 16
 #define ORC_VERIFY_H0 1u
 #define ORC_MAX_MERGE 2u
+#define ORC_RHFG_LITERAL 4u
 
 typedef struct orc_params {
   uint32_t log2_eta, q, r, delta, k, theta, flags;
@@ -108,6 +112,11 @@ ORC_API uint32_t orc_h1(const orc_params* p, const uint32_t* tables, uint32_t oi
   return tabulation(tables, oip) % eta;
 }
 
+/* The shift of window B(i), i >= 1: (i-1)*delta (R2), or i*delta as Eq. 2 prints it. */
+static uint32_t window_shift(const orc_params* p, uint32_t i) {
+  return (i - 1 + ((p->flags & ORC_RHFG_LITERAL) ? 1u : 0u)) * p->delta;
+}
+
 /* RHFG (Eq. 2 with reading R2): RHFG[0](cip) = random hash mod 2^q;
  * RHFG[i](cip) = ((cip >> ((i-1)*delta)) XOR RHFG[0](cip)) mod 2^q. */
 ORC_API void orc_rhfg(const orc_params* p, const uint32_t* tables, uint32_t cip, uint32_t* cols) {
@@ -115,7 +124,7 @@ ORC_API void orc_rhfg(const orc_params* p, const uint32_t* tables, uint32_t cip,
   uint32_t h0 = tabulation(tables + 1024, cip) % C;
   cols[0] = h0;
   for (uint32_t i = 1; i < p->r; ++i) {
-    uint32_t shift = (i - 1) * p->delta;
+    uint32_t shift = window_shift(p, i);
     uint32_t shifted = shift < 32 ? (cip >> shift) : 0u;
     cols[i] = (shifted ^ h0) % C;
   }
@@ -123,7 +132,7 @@ ORC_API void orc_rhfg(const orc_params* p, const uint32_t* tables, uint32_t cip,
 
 /* B(i) window of cip (Eq. 3): q successive bits starting at bit (i-1)*delta. */
 static uint32_t window_of(const orc_params* p, uint32_t cip, uint32_t i) {
-  uint32_t shift = (i - 1) * p->delta;
+  uint32_t shift = window_shift(p, i);
   uint32_t shifted = shift < 32 ? (cip >> shift) : 0u;
   return shifted % (1u << p->q);
 }
@@ -131,7 +140,8 @@ static uint32_t window_of(const orc_params* p, uint32_t cip, uint32_t i) {
 /* Regain a host from a full tuple of columns (R5): B(i) = he_0 XOR he_i
  * (Eq. 3); each bit b of cip is read from the first window B(i) that holds it,
  * then every window of the result must equal B(i). Returns 0 and sets *cip,
- * or -1 when no 32-bit value has these windows. */
+ * or -1 when no 32-bit value has these windows. With ORC_RHFG_LITERAL the bits
+ * no window holds (0..delta-1) are left 0 for the caller to complete. */
 ORC_API int orc_extract(const orc_params* p, const uint32_t* tuple, uint32_t* cip) {
   uint32_t B[ORC_MAX_R];
   for (uint32_t i = 1; i < p->r; ++i) B[i] = tuple[0] ^ tuple[i];
@@ -139,13 +149,13 @@ ORC_API int orc_extract(const orc_params* p, const uint32_t* tuple, uint32_t* ci
   for (uint32_t b = 0; b < 32; ++b) {
     int found = 0;
     for (uint32_t i = 1; i < p->r && !found; ++i) {
-      uint32_t lo = (i - 1) * p->delta;
+      uint32_t lo = window_shift(p, i);
       if (b >= lo && b < lo + p->q) {
         if ((B[i] >> (b - lo)) & 1u) x |= 1u << b;
         found = 1;
       }
     }
-    if (!found) return -1;
+    if (!found && !((p->flags & ORC_RHFG_LITERAL) && b < p->delta)) return -1;
   }
   for (uint32_t i = 1; i < p->r; ++i)
     if (window_of(p, x, i) != B[i]) return -1;
@@ -297,6 +307,15 @@ static void finish_tuple(regain_ctx* g, const uint32_t* tuple) {
   if (rk < g->thr) return;
   uint32_t cip;
   if (orc_extract(g->p, tuple, &cip)) return;
+  if (g->p->flags & ORC_RHFG_LITERAL) {
+    /* bits 0..delta-1 are in no window: every completion whose RHFG[0] is he_0 */
+    for (uint32_t low = 0; low < (1u << g->p->delta); ++low) {
+      uint32_t cols[ORC_MAX_R];
+      orc_rhfg(g->p, g->tables, cip | low, cols);
+      if (cols[0] == tuple[0] && vpush(&g->out, ((uint64_t)(cip | low) << 32) | rk)) g->err = 1;
+    }
+    return;
+  }
   if (g->p->flags & ORC_VERIFY_H0) {
     uint32_t cols[ORC_MAX_R];
     orc_rhfg(g->p, g->tables, cip, cols);

@@ -23,7 +23,7 @@ import weakref
 import numpy as np
 
 from ._abi import (SSD_ECAPACITY, SSD_MAX_GROUP_BITS, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SIDE_CNET,  # noqa: F401
-                   SSD_SIDE_ONET, SSD_SLOT_CHUNKED,
+                   SSD_RHFG_LITERAL, SSD_SIDE_ONET, SSD_SLOT_CHUNKED,
                    SSD_STATUS_CTB_OVERFLOW,
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
                    TUNING_FIELDS, Params, SSDError, Stats, Tuning, check, load)

@@ -15,6 +15,7 @@ SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECAPACITY, SSD_ECUDA, SSD_ETIMEOUT, SSD_ESTA
 SSD_VERIFY_H0 = 1
 SSD_NO_PRUNE = 2
 SSD_SLOT_CHUNKED = 4
+SSD_RHFG_LITERAL = 8
 SSD_MAX_R = 8
 SSD_MAX_ROUTERS = 128
 SSD_SIDE_CNET, SSD_SIDE_ONET = 0, 1

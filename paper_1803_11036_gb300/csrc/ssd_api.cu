@@ -256,7 +256,7 @@ int ssd_params_check(const ssd_params* p) {
   if ((p->r - 2) * p->delta + p->q < 32) return SSD_EINVAL;  // Eq. 2-3: every bit of cip in some B(i)
   if (p->k < 1 || p->k > 65534) return SSD_EINVAL;            // Sec. 3.2: k < 65535
   if (p->theta < 1) return SSD_EINVAL;
-  if (p->flags & ~(SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED)) return SSD_EINVAL;
+  if (p->flags & ~(SSD_VERIFY_H0 | SSD_NO_PRUNE | SSD_SLOT_CHUNKED | SSD_RHFG_LITERAL)) return SSD_EINVAL;
   if (p->ctb_capacity > (1ull << 32) || p->out_capacity > (1ull << 28)) return SSD_EINVAL;
   uint32_t thr;
   return threshold_of(1u << p->log2_eta, p->theta, &thr);
@@ -292,6 +292,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   d.col_mask = (1u << p->q) - 1u;
   d.low_bits = p->q - p->delta;
   d.low_mask = (1u << d.low_bits) - 1u;
+  d.sh0 = (p->flags & SSD_RHFG_LITERAL) ? p->delta : 0u;
   const uint64_t C = 1ull << p->q;
   d.hse_cap = p->hse_capacity ? p->hse_capacity : (uint32_t)(C < 65536 ? C : 65536);
   if (d.hse_cap > C) d.hse_cap = (uint32_t)C;

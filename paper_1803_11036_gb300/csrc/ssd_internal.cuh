@@ -29,6 +29,7 @@ struct Dims {
   uint32_t col_mask;   // 2^q - 1
   uint32_t low_bits;   // q - delta
   uint32_t low_mask;   // 2^(q-delta) - 1
+  uint32_t sh0;        // shift of window B(1): 0, or delta with SSD_RHFG_LITERAL (B(i) at (i-1)*delta + sh0)
   uint32_t hse_cap;    // pool entries per row
   uint64_t ctb_cap;    // tuples per candidate buffer
   uint64_t out_cap;    // staged accepted tuples (a power of two)
@@ -180,7 +181,7 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
   for (uint32_t i = r0; i <= r1; ++i) {
     uint32_t col = c0;
     if (i) {
-      const uint32_t sh = (i - 1u) * d.delta;
+      const uint32_t sh = (i - 1u) * d.delta + d.sh0;
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
@@ -199,7 +200,7 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
   for (uint32_t i = r0; i <= r1; ++i) {
     uint32_t col = c0;
     if (i) {
-      const uint32_t sh = (i - 1u) * d.delta;
+      const uint32_t sh = (i - 1u) * d.delta + d.sh0;
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;

@@ -41,23 +41,26 @@ __device__ __forceinline__ uint32_t tab_hash_global(const uint32_t* T, uint32_t 
          __ldg(T + 768u + (x >> 24));
 }
 
-// The host whose q-bit windows (cip >> (j-1)*delta) mod 2^q are B(j) = he_0 ^ he_j,
-// j = 1..r-1: bits [0, q) from B(1), then the top delta bits of each B(j) at
-// (j-2)*delta + q. Consecutive windows already agree on their overlap, so the
-// only way no host exists is a window bit at position 32 or beyond.
+// The host whose q-bit windows (cip >> ((j-1)*delta + sh0)) mod 2^q are B(j) =
+// he_0 ^ he_j, j = 1..r-1: bits [sh0, sh0 + q) from B(1), then the top delta
+// bits of each B(j) at (j-2)*delta + q + sh0. Consecutive windows already agree
+// on their overlap, so the only way no host exists is a window bit at position
+// 32 or beyond. With sh0 = delta (Eq. 2 as printed) bits 0..delta-1 stay 0: no
+// window holds them.
 __device__ __forceinline__ bool regain_host(const Dims& d, const uint32_t* he, uint32_t* cip) {
+  const uint32_t lim = 32u - d.sh0;   // bits of cip >> sh0
   uint64_t v = he[0] ^ he[1];
   for (uint32_t j = 2; j < d.r; ++j) {
     const uint64_t top = (uint64_t)((he[0] ^ he[j]) >> d.low_bits);
     const uint32_t pos = (j - 2) * d.delta + d.q;
-    if (pos >= 32) {
+    if (pos >= lim) {
       if (top) return false;
     } else {
       v |= top << pos;
     }
   }
-  if (v >> 32) return false;
-  *cip = (uint32_t)v;
+  if (v >> lim) return false;
+  *cip = (uint32_t)(v << d.sh0);
   return true;
 }
 
@@ -302,6 +305,15 @@ __device__ __forceinline__ uint32_t union_rk(const Dims& d, const Scratch& s, ui
   return pc;
 }
 
+// Stage an accepted host with its R_k for the list (warp-wide; ok false = no entry).
+__device__ __forceinline__ void stage_host(const Dims& d, const Scratch& s, bool ok, uint32_t cip, uint32_t pc) {
+  const unsigned long long pos = warp_append(ok, &s.counters->raw);
+  if (ok) {
+    if (pos < d.out_cap) s.stage[pos] = ((unsigned long long)cip << 32) | pc;
+    else atomicOr(&s.counters->status, SSD_STATUS_OUT_OVERFLOW);
+  }
+}
+
 // One candidate tuple c (its pool indices tl, rows 0..i-1) of row level i
 // extended by row-i estimator idx (pool index; kNone when this lane has none):
 // the union test, then the append to the next candidate buffer or, at the last
@@ -331,7 +343,7 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
   } else {
     warp_append(keep, &s.counters->level[i]);
     bool acc = hit && pc >= d.thr;
-    uint32_t cip = 0;
+    uint32_t cip = 0, he0 = 0;
     if (acc) {
       uint32_t he[SSD_MAX_R];
 #pragma unroll
@@ -339,13 +351,19 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
         if (j < i) he[j] = s.pool_col[(uint64_t)j * cap + tl[j]];
       he[i] = s.pool_col[(uint64_t)i * cap + idx];
       acc = regain_host(d, he, &cip);
-      if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he[0];
-      if (acc) acc = view_host_in(view, cip);   // a grouped sketch holds only its group's hosts
+      he0 = he[0];
     }
-    const unsigned long long pos = warp_append(acc, &s.counters->raw);
-    if (acc) {
-      if (pos < d.out_cap) s.stage[pos] = ((unsigned long long)cip << 32) | pc;
-      else atomicOr(&s.counters->status, SSD_STATUS_OUT_OVERFLOW);
+    if (d.sh0 == 0) {
+      if (acc && verify) acc = (tab_hash_global(s.tables + 1024, cip) & d.col_mask) == he0;
+      if (acc) acc = view_host_in(view, cip);   // a grouped sketch holds only its group's hosts
+      stage_host(d, s, acc, cip, pc);
+    } else if (__any_sync(kFull, acc)) {
+      // Eq. 2 as printed: every completion of bits 0..delta-1 whose RHFG[0] is he_0
+      for (uint32_t low = 0; low < (1u << d.delta); ++low) {
+        const uint32_t x = cip | low;
+        const bool ok = acc && (tab_hash_global(s.tables + 1024, x) & d.col_mask) == he0 && view_host_in(view, x);
+        stage_host(d, s, ok, x, pc);
+      }
     }
   }
 }

@@ -20,7 +20,7 @@ __device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t ci
 #pragma unroll
   for (uint32_t i = 1; i < SSD_MAX_R; ++i) {
     if (i < d.r) {
-      const uint32_t sh = (i - 1u) * d.delta;
+      const uint32_t sh = (i - 1u) * d.delta + d.sh0;
       const uint32_t w = sh < 32u ? (cip >> sh) : 0u;
       const uint32_t col = (w ^ c0) & d.col_mask;
       dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = 0;

@@ -91,6 +91,7 @@ extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, 
   d.col_mask = (1u << p->q) - 1u;
   d.low_bits = p->q - p->delta;
   d.low_mask = (1u << d.low_bits) - 1u;
+  d.sh0 = (p->flags & SSD_RHFG_LITERAL) ? p->delta : 0u;
   Plan pl;
   int rc = plan_for(d, pl);
   if (rc != SSD_OK) return rc;

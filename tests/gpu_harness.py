@@ -15,8 +15,13 @@ def to_dev(pairs: np.ndarray):
     return torch.from_numpy(a.view(np.int32)).to("cuda:0")
 
 
+def oracle_flags(flags: int) -> int:
+    """The oracle's flags for a library flag set (the method-changing ones)."""
+    return ((flags & ssd.SSD_VERIFY_H0) and oracle.VERIFY_H0) | ((flags & ssd.SSD_RHFG_LITERAL) and oracle.RHFG_LITERAL)
+
+
 def setup(W: dict, flags: int = 0, **caps):
-    p_or = oracle.params(W["params"], flags & oracle.VERIFY_H0)
+    p_or = oracle.params(W["params"], oracle_flags(flags))
     tabs = tg.hash_tables(W["hash_seed"])
     ctx = ssd.Context(ssd.make_params(W["params"], flags, **caps), tabs)
     return p_or, tabs, ctx

@@ -1,4 +1,5 @@
-"""Accuracy of the GPU detector against exact ground truth, with the paper's rates (Sec. 5):
+"""Accuracy of the GPU detector against exact ground truth, with the paper's rates (Sec. 5), for
+the default reading, the RHFG[0]-checked list and Eq. 2 as printed (SSD_RHFG_LITERAL):
 FPR = hosts reported that are not sliding super points / true sliding super points,
 FNR = sliding super points not reported / true sliding super points, TFR = FPR + FNR.
 Ground truth is the precise algorithm (exact distinct opposite hosts per window). The rates
@@ -31,7 +32,8 @@ def test_fpr_fnr_against_exact_counts(wl):
     tabs = tg.hash_tables(W["hash_seed"])
     T = tg.traffic_for(W)
     k = prm["k"]
-    ctxs = {m: ssd.Context(ssd.make_params(prm, f), tabs) for m, f in (("literal", 0), ("verify", ssd.SSD_VERIFY_H0))}
+    modes = (("literal", 0), ("verify", ssd.SSD_VERIFY_H0), ("eq2_as_printed", ssd.SSD_RHFG_LITERAL))
+    ctxs = {m: ssd.Context(ssd.make_params(prm, f), tabs) for m, f in modes}
     sk = {m: c.sketch() for m, c in ctxs.items()}
     ex = oracle.Exact(k, prm["theta"])
     per = {m: [] for m in ctxs}
@@ -56,5 +58,8 @@ def test_fpr_fnr_against_exact_counts(wl):
     assert out["verify"]["FPR"] <= out["literal"]["FPR"]
     assert out["verify"]["FNR"] >= out["literal"]["FNR"] - 1e-12
     assert out["verify"]["TFR"] < 0.5
+    # Eq. 2 as printed hashes hosts to other estimators, so its rates are reported beside the
+    # others rather than ordered against them
+    assert out["eq2_as_printed"]["TFR"] < 0.5
     for c in ctxs.values():
         c.close()

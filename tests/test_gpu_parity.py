@@ -360,3 +360,28 @@ def test_discrete_window_k1(step):
         nonempty += len(want["ips"]) > 0
     assert nonempty == 5
     run.close()
+
+
+@pytest.mark.parametrize("wl", ["tiny", "paper_c1"])
+@pytest.mark.parametrize("step", ["slot", "fused", "unfused"])
+def test_rhfg_literal_variant(wl, step):
+    """Eq. 2 as printed (SSD_RHFG_LITERAL: windows at i*delta, bits 0..delta-1 completed by the
+    RHFG[0] check) on every path: the merged sketch, the list and R_k equal the oracle's under the
+    same reading; on the separate calls so do the candidate counts and the staged completions."""
+    run = Run(wl, ssd.SSD_RHFG_LITERAL)
+    nonempty = 0
+    for _ in range(min(run.W["slots"], 6)):
+        if step == "slot":
+            got, want = run.step_slot("pruned", with_global=True)
+        elif step == "fused":
+            got, want = run.step_fused("pruned")
+        else:
+            got, want = run.step_unfused("pruned")
+            st = run.ctx.stats()
+            assert st["level"] == [int(x) for x in want["levels"]]
+            assert st["raw"] == want["raw"]
+        assert_list_equal(got, want, f"{wl} slot {run.t}")
+        assert np.array_equal(run.glob.export(), run.pipe.global_sk), run.t
+        nonempty += len(want["ips"]) > 0
+    assert nonempty > 0
+    run.close()

@@ -477,3 +477,55 @@ def test_views_swap_and_partition():
         both = np.concatenate(parts)
         key = lambda a_: a_[:, 0].astype(np.uint64) << np.uint64(32) | a_[:, 1]
         assert np.array_equal(np.sort(key(both)), np.sort(key(pairs)))
+
+
+@pytest.mark.parametrize("p", PARAM_SETS[:3], ids=lambda p: f"q{p.q}r{p.r}d{p.delta}")
+def test_literal_shift_loses_low_bits_and_completion_recovers_them(p):
+    """Eq. 2 as printed (windows at i*delta): hosts that differ only in bits 0..delta-1 share
+    every window B(1..r-1), so no tuple can tell them apart; the extraction fixes bits
+    delta..31 and, among the 2^delta completions, the host is one whose RHFG[0] is he_0."""
+    lit = oracle.Params(*[getattr(p, f) for f in ("log2_eta", "q", "r", "delta", "k", "theta")],
+                        oracle.RHFG_LITERAL)
+    t = tg.hash_tables(77)
+    rng = np.random.default_rng(p.q)
+    low = (1 << p.delta) - 1
+    extra = 0
+    for x in rng.integers(0, 2**32, 300, dtype=np.uint64).astype(np.uint32).tolist():
+        cols = oracle.rhfg(lit, t, x)
+        y = x ^ 1                     # differs in bit 0 only
+        cy = oracle.rhfg(lit, t, y)
+        assert np.array_equal(cols[1:] ^ cols[0], cy[1:] ^ cy[0])
+        prefix = oracle.extract(lit, cols)
+        assert prefix == x & ~low & 0xFFFFFFFF
+        hits = [prefix | v for v in range(1 << p.delta) if oracle.rhfg(lit, t, prefix | v)[0] == cols[0]]
+        assert x in hits
+        extra += len(hits) - 1
+    expected = 300 * ((1 << p.delta) - 1) / (1 << p.q)   # each wrong completion passes with odds 2^-q
+    assert extra < 2 * expected + 30
+
+
+@pytest.mark.parametrize("name,nslots", [("tiny", 6), ("paper_c1", 4)])
+def test_literal_shift_regain_forms_agree(name, nslots):
+    """Under Eq. 2 as printed the recursive, level-wise and pruned regains still agree, and every
+    listed host's tuple of columns (from its own RHFG) has all r estimators hot."""
+    W = tg.workload(name)
+    p = oracle.params(W["params"], oracle.RHFG_LITERAL)
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    pipe = oracle.Pipeline(p, tabs, T.routers)
+    thr, _ = oracle.threshold(p.eta, p.theta)
+    listed = 0
+    for ts in range(nslots):
+        pipe.step(T.slot(ts), regain_method=None)
+        gsk = pipe.global_sk
+        a = oracle.regain(p, tabs, gsk, "recursive")
+        b = oracle.regain(p, tabs, gsk, "levelwise")
+        c = oracle.regain(p, tabs, gsk, "pruned")
+        assert np.array_equal(a["ips"], b["ips"]) and np.array_equal(a["rk"], b["rk"])
+        assert np.array_equal(a["levels"], b["levels"])
+        assert np.array_equal(b["ips"], c["ips"]) and np.array_equal(b["rk"], c["rk"])
+        for x in b["ips"].tolist():
+            cols = oracle.rhfg(p, tabs, x)
+            assert all(oracle.rk_row(p, gsk, i)[cols[i]] >= thr for i in range(p.r))
+        listed += len(b["ips"])
+    assert listed > 0
