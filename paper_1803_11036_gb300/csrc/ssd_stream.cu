@@ -59,10 +59,53 @@ __device__ __forceinline__ uint32_t take_touch(uint8_t* p) {
   return t;
 }
 
-// One estimator of one router, all eta recorders (eta >= 256): optional touch
-// bits applied (tb: this lane's byte of the estimator's touch bits), merged
-// value written to g, "< k" bits to `my` (shared) and counted, recorders
-// advanced. Returns the lane's count of recorders below k.
+// Recorder vectors it0 .. it0+m-1 (m <= 8, 32 lanes x 8 recorders each) of the
+// estimator at `base` and, with TOUCH, their touch bytes. All loads of a group
+// are issued before any store of it (a store in between could alias the next
+// load and serialise them).
+template <bool TOUCH>
+__device__ __forceinline__ void load_group(const uint4* r0, uint64_t base, const uint8_t* tb, uint32_t it0, uint32_t m,
+                                           int lane, uint4 (&v)[8], uint32_t (&t)[8]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (u < (int)m) {
+      v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
+      if (TOUCH) t[u] = tb[(it0 + u) * 32];
+    }
+  }
+}
+
+// The loaded group: touch bits applied (and cleared), merged value written to
+// g, "< k" bits to `my` (shared) and counted, recorders advanced. Returns the
+// lane's count of recorders below k in the group.
+template <bool ADV, bool HOT, bool TOUCH>
+__device__ __forceinline__ uint32_t proc_group(uint4* r0, uint4* g, uint64_t base, uint8_t* tb, uint8_t* my,
+                                               uint32_t it0, uint32_t m, int lane, uint32_t kk, uint4 (&v)[8],
+                                               const uint32_t (&t)[8]) {
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (u < (int)m) {
+      const uint64_t at = base + (it0 + u) * 32 + lane;
+      if (TOUCH && t[u]) {
+        v[u] = apply8(v[u], t[u]);
+        tb[(it0 + u) * 32] = 0;
+      }
+      if (g) __stcs(g + at, v[u]);
+      if (HOT) {
+        const uint32_t bits = lt8(v[u], kk);
+        cnt += __popc(bits);
+        my[(it0 + u) * 32 + lane] = (uint8_t)bits;
+      }
+      if (ADV) __stcs(r0 + at, inc8(v[u]));
+    }
+  }
+  return cnt;
+}
+
+// One estimator of one router, all eta recorders (eta >= 256), in groups of 8
+// vectors: load_group then proc_group. tb: this lane's byte of the estimator's
+// touch bits. Returns the lane's count of recorders below k.
 template <bool ADV, bool HOT, bool TOUCH>
 __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint4* g, uint64_t base, uint8_t* tb,
                                                   uint8_t* my, int lane) {
@@ -73,31 +116,8 @@ __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint
     const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
     uint4 v[8];
     uint32_t t[8];
-    // all loads first (a store in between could alias the next load and serialise them)
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (u < (int)m) {
-        v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
-        if (TOUCH) t[u] = tb[(it0 + u) * 32];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (u < (int)m) {
-        const uint64_t at = base + (it0 + u) * 32 + lane;
-        if (TOUCH && t[u]) {
-          v[u] = apply8(v[u], t[u]);
-          tb[(it0 + u) * 32] = 0;
-        }
-        if (g) __stcs(g + at, v[u]);
-        if (HOT) {
-          const uint32_t bits = lt8(v[u], kk);
-          cnt += __popc(bits);
-          my[(it0 + u) * 32 + lane] = (uint8_t)bits;
-        }
-        if (ADV) __stcs(r0 + at, inc8(v[u]));
-      }
-    }
+    load_group<TOUCH>(r0, base, tb, it0, m, lane, v, t);
+    cnt += proc_group<ADV, HOT, TOUCH>(r0, g, base, tb, my, it0, m, lane, kk, v, t);
   }
   return cnt;
 }
@@ -252,9 +272,13 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
 // (warp e takes vectors e*32 + lane, e*32 + lane + 32*count, ...), so every lane
 // of a warp runs the same iterations, as combine mode 1 needs.
 template <bool NEXT, bool PACKED, int CM>
-__global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, const Scratch s,
+__global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch s,
                                                               const __grid_constant__ ChunkArgs a) {
   constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
+  // Programmatic dependent launch: the next chunk's grid may be scheduled now (its blocks take
+  // SM slots only as this grid's blocks exit); everything below the wait reads what the
+  // previous chunk wrote (this chunk's touch bits) or writes what it read (the next buffer).
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ __align__(16) uint32_t smc[];
   uint32_t* sT = smc;                                              // 2048 table words
   uint8_t* masks = reinterpret_cast<uint8_t*>(smc + (TABLES ? 2048 : 0));
@@ -264,6 +288,18 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
     for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = s.tables[i];
     __syncthreads();
   }
+  // the warp's first estimator: its recorders are loaded before the wait (no earlier grid of
+  // the slot writes them), its touch bytes after it
+  const uint32_t iters = d.eta >> 8;
+  const uint32_t m0 = iters < 8u ? iters : 8u;
+  const uint64_t tstep = d.eta >> 3;   // touch bytes per estimator
+  uint4 v[8];
+  uint32_t t[8];
+  const uint64_t e_first = (uint64_t)blockIdx.x * (kBlock / 32) + wid;
+  if (e_first < a.count)
+    load_group<false>(reinterpret_cast<const uint4*>(a.router), ((a.se0 + e_first) << d.log2_eta) >> 3, nullptr, 0,
+                      m0, lane, v, t);
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous grid has completed
   const uint32_t nr0 = NEXT ? (uint32_t)(a.nx_se0 >> d.q) : 0u;
   const uint32_t nr1 = NEXT ? (uint32_t)((a.nx_se0 + a.nx_count - 1) >> d.q) : 0u;
   const uint64_t slots = a.count * 32;   // (estimator, lane) slots sharing the pairs
@@ -281,14 +317,10 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
       touch_pair<CM>(a.next, 0, c1, o1, live && in1, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
   };
-  for (uint64_t e = (uint64_t)blockIdx.x * (kBlock / 32) + wid; e < a.count; e += wstride) {
-    const uint64_t se = a.se0 + e;
-    uint8_t* tb = a.touch + e * (d.eta >> 3) + lane;
-    // this slot's first pair vector is loaded before the estimator so the two loads overlap
+  const uint32_t kk = d.k | (d.k << 16);
+  // after an estimator's pass: its share of the next chunk's touches, then its pooling
+  auto finish = [&](uint64_t e, uint64_t se, uint32_t cnt, uint4 w0) {
     const uint64_t vb0 = e * 32;
-    uint4 w0 = make_uint4(0, 0, 0, 0);
-    if (NEXT && vb0 + lane < a.nvec) w0 = __ldcs(a.vec + vb0 + lane);
-    const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, tb, my, lane);
     if (NEXT) {
       if (vb0 < a.nvec) touch2(w0, vb0 + lane < a.nvec);
       for (uint64_t vb = vb0 + slots; vb < a.nvec; vb += slots) {
@@ -307,6 +339,35 @@ __global__ void __launch_bounds__(kBlock, NEXT ? 3 : 4) k_chunk(const Dims d, co
       }
     }
     pool_if_hot(d, s, se, cnt, my, lane);
+  };
+  // this slot's first pair vector of an estimator is loaded before its pass so the loads overlap
+  auto first_pair = [&](uint64_t e) {
+    return (NEXT && e * 32 + lane < a.nvec) ? __ldcs(a.vec + e * 32 + lane) : make_uint4(0, 0, 0, 0);
+  };
+  uint64_t e = e_first;
+  if (e < a.count) {   // the prefetched first group, then any further groups
+    const uint64_t se = a.se0 + e;
+    uint8_t* tb = a.touch + e * tstep + lane;
+    const uint4 w0 = first_pair(e);
+    const uint64_t base = (se << d.log2_eta) >> 3;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < (int)m0) t[u] = tb[u * 32];
+    uint32_t cnt = proc_group<true, true, true>(r0, g, base, tb, my, 0, m0, lane, kk, v, t);
+    for (uint32_t it0 = 8; it0 < iters; it0 += 8) {
+      const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
+      load_group<true>(r0, base, tb, it0, m, lane, v, t);
+      cnt += proc_group<true, true, true>(r0, g, base, tb, my, it0, m, lane, kk, v, t);
+    }
+    finish(e, se, cnt, w0);
+    e += wstride;
+  }
+  for (; e < a.count; e += wstride) {
+    const uint64_t se = a.se0 + e;
+    const uint4 w0 = first_pair(e);
+    const uint32_t cnt =
+        one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, a.touch + e * tstep + lane, my, lane);
+    finish(e, se, cnt, w0);
   }
 }
 
@@ -376,8 +437,18 @@ cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArg
   const uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
   uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED, CM>, smem, tn);
   if (grid > need) grid = need;
-  k_chunk<NEXT, PACKED, CM><<<(unsigned)grid, kBlock, smem, st>>>(d, s, a);
-  return cudaGetLastError();
+  // launched as a programmatic dependent of the previous kernel on the stream (see k_chunk)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_chunk<NEXT, PACKED, CM>, d, s, a);
 }
 
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
