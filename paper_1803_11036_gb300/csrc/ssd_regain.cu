@@ -5,16 +5,18 @@
 //   is kept only when the union of its two estimators still has R_k >= the
 //   threshold: the union is an elementwise maximum, so R_k = popcount of the
 //   AND of the "recorder < k" bitmaps, and it can only fall as rows are added;
-//   a dropped tuple would fail the final test. Computed as a 32 x 32 tile of
-//   AND-popcounts per block with the bitmaps staged in shared memory.
+//   a dropped tuple would fail the final test. Computed as 64 x 64 tiles of
+//   AND-popcounts (4 x 4 per thread, one carry-save step per two words) with
+//   the bitmaps staged in shared memory and one append per tile.
 // Level i >= 2: the overlap test fixes the low q-delta bits of he_i
 //   (B(i) mod 2^(q-delta) = B(i-1) >> delta with B(j) = he_0 XOR he_j), so the
 //   only row-i estimators a candidate can extend to are the hot ones with those
 //   low bits. The k_pairs launch also buckets each row's hot estimators by their
 //   low q-delta bits, and a candidate reads its one bucket (when 2^(q-delta) is
 //   too large for the index, it probes the 2^delta columns in hot_idx instead).
-//   Hits are tested by the whole warp (coalesced bitmap reads) and survivors
-//   are appended with warp-aggregated atomics.
+//   Hits are tested by groups of four lanes (up to eight at once per warp, all
+//   loads of a group's share issued together) and survivors are appended with
+//   warp-aggregated atomics.
 // The last level applies the final test (R_k of the full union), regains the
 //   host from B(1..r-1) and stages (cip, R_k); one block then sorts the staged
 //   entries and writes the ascending, duplicate-free list.
@@ -510,23 +512,30 @@ __global__ void __launch_bounds__(kListThreads) k_list(const Dims d, const Scrat
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
                                unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches,
                                uint32_t view) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kSmemKeys * sizeof(unsigned long long)));
+  // k_list's dynamic shared memory limit and k_pairs' occupancy, once per device
+  constexpr int kDevices = 64;
+  static bool attr[kDevices] = {};
+  static int pair_bps_of[kDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    e = cudaFuncSetAttribute(k_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemKeys * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[dev] = true;
   }
-  static int pair_bps = 0;   // resident k_pairs blocks per SM
+  int& pair_bps = pair_bps_of[dev];   // resident k_pairs blocks per SM
   if (!pair_bps) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pair_bps, k_pairs, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pair_bps, k_pairs, kBlock, 0);
     if (e != cudaSuccess) return e;
     if (pair_bps < 1) pair_bps = 1;
   }
   const uint32_t pair_blocks = (uint32_t)(sms * pair_bps);
   const uint32_t bucket_blocks = s.bucket_off && d.r > 2 ? d.r - 2 : 0;
   k_pairs<<<pair_blocks + bucket_blocks, kBlock, 0, st>>>(d, s, pair_blocks);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *launches += 1;
   for (uint32_t i = 2; i < d.r; ++i) {

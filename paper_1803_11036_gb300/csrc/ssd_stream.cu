@@ -273,11 +273,12 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
 // of a warp runs the same iterations, as combine mode 1 needs.
 template <bool NEXT, bool PACKED, int CM>
 __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch s,
-                                                              const __grid_constant__ ChunkArgs a) {
+                                                     const __grid_constant__ ChunkArgs a) {
   constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
   // Programmatic dependent launch: the next chunk's grid may be scheduled now (its blocks take
-  // SM slots only as this grid's blocks exit); everything below the wait reads what the
-  // previous chunk wrote (this chunk's touch bits) or writes what it read (the next buffer).
+  // SM slots only as this grid's blocks exit). After the wait below, this grid reads what the
+  // previous chunk wrote (this chunk's touch bits) and sets bits in the buffer the previous
+  // chunk was applying and clearing (the next chunk's).
   asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ __align__(16) uint32_t smc[];
   uint32_t* sT = smc;                                              // 2048 table words
