@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -495,6 +496,16 @@ def run_ours(args, world, rank, local):
     all_pk = sum_over_ranks(timed_pk, world)
     value = all_pk / (max_ms / 1e3) / 1e6
 
+    # ---- realised column load: each row's mean R_k after the last close, through Eq. 1
+    occ = routers[0].occupancy(stream)
+    C_cols, eta_ = 1 << prm["q"], 1 << prm["log2_eta"]
+    mean_rk = [o / C_cols for o in occ]
+    load = [round(-eta_ * math.log(1.0 - m / eta_), 1) for m in mean_rk]
+    column_load = {"mean_rk_per_row": [round(m, 2) for m in mean_rk], "eq1_distinct_per_column": load,
+                   "theta_over_4": prm["theta"] / 4,
+                   "note": "router sketch after the last timed slot's close; a column nearing theta/4 turns "
+                           "most estimators hot"}
+
     # ---- the same slots under the default launch configuration, for the tuner's record
     default_leg = None
     tuned = ctx.tuning
@@ -687,6 +698,7 @@ def run_ours(args, world, rank, local):
                      "algorithmic_bytes_per_pass": pass_bytes,
                      "traffic": traffic},
         "hot_per_row": st["hot"], "candidates_per_level": st["level"], "list_size": st["n_out"],
+        "column_load": column_load,
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,

@@ -170,6 +170,12 @@ SSD_API int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot);
 #define SSD_MAX_GROUP_BITS 16
 SSD_API int ssd_sketch_set_view(ssd_sketch* s, uint32_t side, uint32_t group_bits, uint32_t group);
 SSD_API int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group_bits, uint32_t* group);
+/* Occupancy of a sketch (diagnostics, not on the slot path): rk_sum[i] (host,
+ * r entries) receives the sum over row i's 2^q estimators of R_k, the recorders
+ * below k (Sec. 3.2). A row's mean R_k gives through Eq. 1 the distinct opposite
+ * hosts its columns hold, the realised column load. Reads the whole RSEA once
+ * and waits for `stream`. */
+SSD_API int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream);
 /* Copy `count` recorders starting at recorder `first` to dst (host or device).
  * Waits for `stream` before returning. Checkpointing a sketch is
  * export + ssd_sketch_slot; resuming is import. */

@@ -22,7 +22,7 @@ import weakref
 
 import numpy as np
 
-from ._abi import (SSD_ECAPACITY, SSD_MAX_GROUP_BITS, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SIDE_CNET,  # noqa: F401
+from ._abi import (SSD_ECAPACITY, SSD_MAX_GROUP_BITS, SSD_MAX_R, SSD_MAX_ROUTERS, SSD_NO_PRUNE, SSD_SIDE_CNET,  # noqa: F401
                    SSD_RHFG_LITERAL, SSD_SIDE_ONET, SSD_SLOT_CHUNKED,
                    SSD_STATUS_CTB_OVERFLOW,
                    SSD_STATUS_HSE_OVERFLOW, SSD_STATUS_LIST_OVERFLOW, SSD_STATUS_OUT_OVERFLOW, SSD_VERIFY_H0,
@@ -115,6 +115,13 @@ class Sketch:
         whose top group_bits bits are `group`. Before the sketch's first scan."""
         check(self.ctx.L.ssd_sketch_set_view(self._h, side, group_bits, group), "ssd_sketch_set_view")
         return self
+
+    def occupancy(self, stream=None) -> list[int]:
+        """Per row, the sum over its estimators of R_k (recorders below k); see ssd_sketch_occupancy."""
+        out = (ctypes.c_uint64 * SSD_MAX_R)()
+        check(self.ctx.L.ssd_sketch_occupancy(self._h, out, _stream_handle(stream, self.ctx.device)),
+              "ssd_sketch_occupancy")
+        return [int(x) for x in out[: self.ctx.params.r]]
 
     def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
         """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""

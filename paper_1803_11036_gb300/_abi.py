@@ -63,6 +63,7 @@ SIGNATURES = {
     "ssd_sketch_set_slot": ([_vp, _u64], _int),
     "ssd_sketch_set_view": ([_vp, _u32, _u32, _u32], _int),
     "ssd_sketch_view": ([_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _int),
+    "ssd_sketch_occupancy": ([_vp, ctypes.POINTER(_u64), _vp], _int),
     "ssd_sketch_export": ([_vp, _u64, _u64, _vp, _vp], _int),
     "ssd_sketch_import": ([_vp, _vp, _u64, _vp], _int),
     "ssd_scan": ([_vp, _vp, _u64, _vp], _int),

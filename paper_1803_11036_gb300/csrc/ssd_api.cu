@@ -428,6 +428,25 @@ int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group_bits, u
   return SSD_OK;
 }
 
+int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream) {
+  if (!s || !rk_sum) return SSD_EINVAL;
+  ssd_ctx* ctx = s->ctx;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  // the list staging buffer (at least 2^20 words) holds the r totals: this call is ordered on the
+  // context's one stream like a regain
+  unsigned long long* acc = ctx->stage;
+  SSD_CUDA(cudaMemsetAsync(acc, 0, SSD_MAX_R * sizeof(unsigned long long), st));
+  cudaError_t e = ssd::launch_occupancy(ctx->d, s->dr, acc, ctx->sms, st);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy kernel");
+  ctx->launches += 1;
+  unsigned long long h[SSD_MAX_R];
+  SSD_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SSD_CUDA(cudaStreamSynchronize(st));
+  for (uint32_t i = 0; i < ctx->d.r; ++i) rk_sum[i] = h[i];
+  return SSD_OK;
+}
+
 int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
   if (!s || (count && !dst)) return SSD_EINVAL;
   const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;

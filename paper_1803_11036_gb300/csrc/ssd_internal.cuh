@@ -240,6 +240,11 @@ struct ChunkArgs {
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st);
 
+// ---- diagnostics (ssd_diag.cu) ----
+// rk_sum[i] += sum over row i's estimators of R_k (recorders below k); eta >= 8.
+cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, unsigned long long* rk_sum, int sms,
+                             cudaStream_t st);
+
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.
 // `view`: the regained sketch's view; hosts outside its group are not listed.

@@ -122,7 +122,7 @@ __device__ __forceinline__ uint32_t csa_pop(uint32_t& ones, uint32_t a, uint32_t
 // output columns interleaved by 16 so the shared-memory reads are free of bank
 // conflicts); with the bucket index, block pair_blocks + m builds the buckets of
 // row 2 + m.
-__global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s, uint32_t pair_blocks) {
+__global__ void __launch_bounds__(kBlock, 3) k_pairs(const Dims d, const Scratch s, uint32_t pair_blocks) {
   if (blockIdx.x >= pair_blocks) {
     build_buckets(d, s, 2 + (blockIdx.x - pair_blocks));
     return;
@@ -150,11 +150,34 @@ __global__ void __launch_bounds__(kBlock) k_pairs(const Dims d, const Scratch s,
       for (uint32_t k0 = 0; k0 < d.words; k0 += KW) {
         const uint32_t kw = d.words - k0 < (uint32_t)KW ? d.words - k0 : (uint32_t)KW;
         __syncthreads();
-        for (int e = threadIdx.x; e < TA * KW; e += kBlock) {
-          const int rr = e / KW, cc = e % KW;
-          const bool in = cc < (int)kw;   // words past kw are staged as 0
-          A[rr][cc] = (in && a0 + rr < n0) ? bm0[(uint64_t)(a0 + rr) * d.words + k0 + cc] : 0u;
-          B[rr][cc] = (in && b0 + rr < n1) ? bm1[(uint64_t)(b0 + rr) * d.words + k0 + cc] : 0u;
+        if ((d.words & 3u) == 0) {
+          // 16-byte loads, all eight of a thread issued before any store (one round trip)
+          constexpr int kVec = TA * KW / 4 / kBlock;   // 16-byte vectors per thread per operand
+          uint4 va[kVec], vb[kVec];
+#pragma unroll
+          for (int q = 0; q < kVec; ++q) {
+            const int e = threadIdx.x + q * kBlock, rr = e / (KW / 4), c4 = (e % (KW / 4)) * 4;
+            const bool in = c4 < (int)kw;   // words past kw are staged as 0
+            va[q] = (in && a0 + rr < n0)
+                        ? *reinterpret_cast<const uint4*>(bm0 + (uint64_t)(a0 + rr) * d.words + k0 + c4)
+                        : make_uint4(0, 0, 0, 0);
+            vb[q] = (in && b0 + rr < n1)
+                        ? *reinterpret_cast<const uint4*>(bm1 + (uint64_t)(b0 + rr) * d.words + k0 + c4)
+                        : make_uint4(0, 0, 0, 0);
+          }
+#pragma unroll
+          for (int q = 0; q < kVec; ++q) {
+            const int e = threadIdx.x + q * kBlock, rr = e / (KW / 4), c4 = (e % (KW / 4)) * 4;
+            A[rr][c4] = va[q].x; A[rr][c4 + 1] = va[q].y; A[rr][c4 + 2] = va[q].z; A[rr][c4 + 3] = va[q].w;
+            B[rr][c4] = vb[q].x; B[rr][c4 + 1] = vb[q].y; B[rr][c4 + 2] = vb[q].z; B[rr][c4 + 3] = vb[q].w;
+          }
+        } else {
+          for (int e = threadIdx.x; e < TA * KW; e += kBlock) {
+            const int rr = e / KW, cc = e % KW;
+            const bool in = cc < (int)kw;   // words past kw are staged as 0
+            A[rr][cc] = (in && a0 + rr < n0) ? bm0[(uint64_t)(a0 + rr) * d.words + k0 + cc] : 0u;
+            B[rr][cc] = (in && b0 + rr < n1) ? bm1[(uint64_t)(b0 + rr) * d.words + k0 + cc] : 0u;
+          }
         }
         __syncthreads();
         for (uint32_t cc = 0; cc < kw; cc += 2) {

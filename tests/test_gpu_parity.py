@@ -385,3 +385,17 @@ def test_rhfg_literal_variant(wl, step):
         nonempty += len(want["ips"]) > 0
     assert nonempty > 0
     run.close()
+
+
+@pytest.mark.parametrize("wl", ["tiny", "paper_c1"])
+def test_occupancy_equals_oracle_rk_sums(wl):
+    """ssd_sketch_occupancy: per row, the sum of R_k over the row's estimators, for the merged
+    sketch and every router, equal to the oracle's rows of R_k summed."""
+    run = Run(wl)
+    for _ in range(3):
+        run.step_unfused("pruned")
+    rows = range(run.p.r)
+    assert run.glob.occupancy() == [int(oracle.rk_row(run.p, run.pipe.global_sk, i).sum()) for i in rows]
+    for r_gpu, r_or in zip(run.routers, run.pipe.routers):
+        assert r_gpu.occupancy() == [int(oracle.rk_row(run.p, r_or, i).sum()) for i in rows]
+    run.close()
