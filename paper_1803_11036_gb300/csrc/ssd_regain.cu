@@ -66,6 +66,31 @@ __device__ __forceinline__ bool regain_host(const Dims& d, const uint32_t* he, u
   return true;
 }
 
+// Each tail kernel is launched as a programmatic dependent of the kernel before it
+// on the stream: it lets its own successor be scheduled at once, then waits (in
+// hardware) until its predecessor has completed - it reads the counters and
+// buffers that kernel wrote - so only the launch latency is overlapped.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Row i's pooled hot estimators bucketed by the low q-delta bits of their column
 // (one block; counting sort in global memory: count, exclusive scan, fill). The
 // order inside a bucket is that of the fill's atomics; the levels do not depend
@@ -123,6 +148,7 @@ __device__ __forceinline__ uint32_t csa_pop(uint32_t& ones, uint32_t a, uint32_t
 // conflicts); with the bucket index, block pair_blocks + m builds the buckets of
 // row 2 + m.
 __global__ void __launch_bounds__(kBlock, 3) k_pairs(const Dims d, const Scratch s, uint32_t pair_blocks) {
+  pdl_enter();
   if (blockIdx.x >= pair_blocks) {
     build_buckets(d, s, 2 + (blockIdx.x - pair_blocks));
     return;
@@ -412,6 +438,7 @@ __device__ __forceinline__ uint32_t load_candidate(const Dims& d, const Scratch&
 __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s, const uint32_t i,
                                                   const uint32_t* __restrict__ rctb, uint32_t* __restrict__ sctb,
                                                   const uint32_t view) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const unsigned long long avail = s.counters->level[i - 1];
   const uint64_t nc = avail < d.ctb_cap ? avail : d.ctb_cap;
@@ -474,6 +501,7 @@ __device__ void bitonic(unsigned long long* keys, uint32_t P) {
 // cip (its largest R_k), and write the list when it fits the caller's capacity.
 __global__ void __launch_bounds__(kListThreads) k_list(const Dims d, const Scratch s, uint32_t* ips, uint32_t* rk,
                                                        uint64_t cap, unsigned long long* n_out_dev) {
+  pdl_enter();
   extern __shared__ unsigned long long skeys[];
   __shared__ unsigned int warp_cnt[kListThreads / 32];
   __shared__ unsigned long long running;
@@ -557,22 +585,20 @@ cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, u
   }
   const uint32_t pair_blocks = (uint32_t)(sms * pair_bps);
   const uint32_t bucket_blocks = s.bucket_off && d.r > 2 ? d.r - 2 : 0;
-  k_pairs<<<pair_blocks + bucket_blocks, kBlock, 0, st>>>(d, s, pair_blocks);
-  e = cudaGetLastError();
+  e = launch_pdl(k_pairs, pair_blocks + bucket_blocks, kBlock, 0, st, d, s, pair_blocks);
   if (e != cudaSuccess) return e;
   *launches += 1;
   for (uint32_t i = 2; i < d.r; ++i) {
     // level 1 (pairs) wrote ctb[0]; level i reads ctb[i & 1] and writes ctb[(i + 1) & 1]
     const uint32_t* rctb = s.ctb[i & 1];
     uint32_t* sctb = s.ctb[(i + 1) & 1];
-    k_level<<<sms * 8, kBlock, 0, st>>>(d, s, i, rctb, sctb, view);
-    e = cudaGetLastError();
+    e = launch_pdl(k_level, (unsigned)(sms * 8), kBlock, 0, st, d, s, i, rctb, sctb, view);
     if (e != cudaSuccess) return e;
     *launches += 1;
   }
-  k_list<<<1, kListThreads, kSmemKeys * sizeof(unsigned long long), st>>>(d, s, ips, rk, cap, n_out_dev);
+  e = launch_pdl(k_list, 1, kListThreads, kSmemKeys * sizeof(unsigned long long), st, d, s, ips, rk, cap, n_out_dev);
   *launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace ssd
