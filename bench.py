@@ -171,10 +171,39 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def _code_tokens(text: str) -> str:
+    """C/CUDA source without comments and whitespace (string literals kept as written), so that a
+    comment or layout edit leaves the kernel's hash alone."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif c.isspace():
+            out.append(" ")
+            while i < n and text[i].isspace():
+                i += 1
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
 def kernel_source_hash() -> str:
+    """Hash of the chunk kernel's sources (code only) for matching a committed profile."""
     h = hashlib.sha256()
     for f in ("ssd_stream.cu", "ssd_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1803_11036_gb300", "csrc", f), "rb").read())
+        h.update(_code_tokens(open(os.path.join(ROOT, "paper_1803_11036_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

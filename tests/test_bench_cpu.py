@@ -1,0 +1,48 @@
+"""bench.py's contract on the CPU: the reference arm (the oracle timed on the host) prints one JSON
+line with every key the contract names; the committed chunk profile's DRAM traffic is used only
+while the kernel's code and the launch's chunk size match it; comments and layout do not count as
+code for that match."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "Mpps" and d["steps"] == 2
+    assert d["higher_is_better"] is True and d["config"]["workload"] == "corelink_c2"
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Mpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_profile_traffic_needs_matching_code_and_chunk():
+    t = bench.profiled_traffic("corelink_c2", 131072)
+    assert t is not None and 1.0e9 < t < 1.3e9   # ~1.054 x the 1.074 GB a chunk launch must move
+    assert bench.profiled_traffic("corelink_c2", 262144) is None
+    assert bench.profiled_traffic("no_such_workload", 131072) is None
+
+
+def test_code_tokens_ignore_comments_not_strings():
+    a = bench._code_tokens('int a; // note\n/* block\n */ asm("x; // kept");\n\n  int   b;')
+    b = bench._code_tokens('int a;\nasm("x; // kept"); int b;')
+    assert a == b
+    assert bench._code_tokens('asm("x");') != bench._code_tokens('asm("y");')
+
+
+def test_gbps_conventions():
+    g = bench.gbps(1000.0)          # 1 Gpps of 800-byte packets
+    assert g["si"] == 6400.0 and g["paper_convention"] == 6250.0
