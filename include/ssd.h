@@ -367,6 +367,14 @@ SSD_API int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_
                          const uint64_t* n_pairs, int n, ssd_sketch* global, int reps, ssd_tuning* out,
                          void* stream);
 
+/* A counter the context increments whenever it frees or replaces a device
+ * buffer that work captured in a CUDA graph may reference: the touch-bit buffers
+ * (ssd_tuning_set with a new touch_chunk_bytes, ssd_autotune), the pre-hashed
+ * pairs and the host staging areas (ssd_reserve, or an ssd_slot / ssd_slot_host
+ * with a larger slot than any before). A graph captured at epoch e may be
+ * replayed only while the epoch is still e. Host only; 0 for NULL. */
+SSD_API uint64_t ssd_buffer_epoch(const ssd_ctx* ctx);
+
 /* Counters of the context's last regain or close (waits for `stream`). */
 SSD_API int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream);
 

@@ -438,9 +438,14 @@ class SlotGraph:
             r.slot = v
         if global_sketch is not None:
             global_sketch.slot = gslot
+        self._epoch = int(ctx.L.ssd_buffer_epoch(ctx._h))
 
     def replay(self) -> None:
-        """Run the captured slot on the current contents of `inputs` (asynchronous)."""
+        """Run the captured slot on the current contents of `inputs` (asynchronous). Refuses when
+        the context has replaced a buffer the graph holds since the capture (ssd_buffer_epoch)."""
+        if int(self.ctx.L.ssd_buffer_epoch(self.ctx._h)) != self._epoch:
+            raise RuntimeError("the context replaced buffers this graph holds (a new touch chunk size, "
+                               "ssd_reserve or a larger slot); capture the slot again")
         merged = self.routers[0].slot
         self.graph.replay()
         for r in self.routers:

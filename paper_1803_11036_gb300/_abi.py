@@ -82,6 +82,7 @@ SIGNATURES = {
     "ssd_autotune": ([_vp, _vp, _vp, _vp, _int, _vp, _int, ctypes.POINTER(Tuning), _vp], _int),
     "ssd_set_trace": ([_vp, _vp, _vp, _vp], _int),
     "ssd_stats_get": ([_vp, ctypes.POINTER(Stats), _vp], _int),
+    "ssd_buffer_epoch": ([_vp], _u64),
     "ssd_launch_count": ([_vp], _u64),
     "ssd_strerror": ([_int], ctypes.c_char_p),
     "ssd_last_cuda_error": ([], ctypes.c_char_p),

@@ -47,6 +47,7 @@ struct ssd_ctx {
   uint64_t hs_bytes;
   uint64_t hs_calls;
   cudaEvent_t ev_hs_free[2], ev_hs_copied;
+  uint64_t epoch;   // ssd_buffer_epoch: bumped when a buffer captured work may hold is replaced
 };
 
 struct ssd_sketch {
@@ -645,6 +646,7 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
     SSD_CUDA(cudaStreamSynchronize(st));
     cudaFree(ctx->packed);
     ctx->packed = nullptr;
+    ctx->epoch += 1;
     const uint64_t want = n_pairs + n_pairs / 4 + 64;
     if (cudaMalloc(&ctx->packed, want * 8) != cudaSuccess) {
       cudaGetLastError();
@@ -824,6 +826,7 @@ int ssd_slot_host(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* cons
       cudaFree(ctx->hs_buf[i]);
       ctx->hs_buf[i] = nullptr;
     }
+    ctx->epoch += 1;
     const uint64_t want = off[n] + off[n] / 4 + 256;
     for (int i = 0; i < 2; ++i) {
       if (cudaMalloc(&ctx->hs_buf[i], want) != cudaSuccess) {
@@ -859,6 +862,7 @@ int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs) {
   if (max_pairs > ctx->packed_cap) {
     cudaFree(ctx->packed);
     ctx->packed = nullptr;
+    ctx->epoch += 1;
     if (cudaMalloc(&ctx->packed, max_pairs * 8) != cudaSuccess) {
       cudaGetLastError();
       ctx->packed_cap = 0;
@@ -868,6 +872,7 @@ int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs) {
   }
   const uint64_t bytes = ((max_pairs * 8 + 15) & ~15ull) + 256;
   if (bytes > ctx->hs_bytes) {
+    ctx->epoch += 1;
     for (int i = 0; i < 2; ++i) {
       cudaFree(ctx->hs_buf[i]);
       ctx->hs_buf[i] = nullptr;
@@ -902,6 +907,8 @@ int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
 }
 
 uint64_t ssd_launch_count(const ssd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+uint64_t ssd_buffer_epoch(const ssd_ctx* ctx) { return ctx ? ctx->epoch : 0; }
 
 int ssd_tuning_get(const ssd_ctx* ctx, ssd_tuning* out) {
   if (!ctx || !out) return SSD_EINVAL;
@@ -948,6 +955,7 @@ int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
       ctx->touch[i] = nb[i];
     }
     ctx->touch_bytes = bytes;
+    ctx->epoch += 1;
   }
   ctx->tn.stream_bps = t->stream_blocks_per_sm;
   ctx->tn.scan_bps = t->scan_blocks_per_sm;

@@ -31,6 +31,7 @@ int main(void) {
   if (ssd_params_check(&bad) != SSD_EINVAL) return fail("bad params accepted", SSD_EINVAL);
   if (ssd_create(NULL, NULL, 0, NULL) != SSD_EINVAL) return fail("null create accepted", SSD_EINVAL);
   if (ssd_sketch_set_view(NULL, SSD_SIDE_CNET, 0, 0) != SSD_EINVAL) return fail("null view", SSD_EINVAL);
+  if (ssd_buffer_epoch(NULL) != 0 || ssd_launch_count(NULL) != 0) return fail("null counters", SSD_EINVAL);
   printf("refusals ok\n");
 
   return 0;

@@ -47,3 +47,24 @@ def test_captured_slot_equals_direct_calls(wl, flags, with_global):
         assert np.array_equal(x.export(), y.export()) and x.slot == y.slot == W["slots"]
     ctx_a.close()
     ctx_b.close()
+
+
+def test_replay_refused_after_buffers_replaced():
+    """A graph holds the context's touch buffers: once ssd_tuning_set replaces them (a new touch
+    chunk size), ssd_buffer_epoch has moved and SlotGraph.replay refuses instead of running on
+    freed memory."""
+    W = tg.workload("paper_c1")
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    ctx = ssd.Context(ssd.make_params(W["params"]), tabs)
+    routers = [ctx.sketch()]
+    graph = ssd.SlotGraph(ctx, routers, [T.count(0, 0)])
+    graph.inputs[0].copy_(to_dev(T.slot(0)[0]))
+    graph.replay()
+    graph.result()
+    e0 = int(ctx.L.ssd_buffer_epoch(ctx._h))
+    ctx.tuning = dict(touch_chunk_bytes=16 << 20)
+    assert int(ctx.L.ssd_buffer_epoch(ctx._h)) == e0 + 1
+    with pytest.raises(RuntimeError):
+        graph.replay()
+    ctx.close()
