@@ -443,6 +443,9 @@ class SlotGraph:
     def replay(self) -> None:
         """Run the captured slot on the current contents of `inputs` (asynchronous). Refuses when
         the context has replaced a buffer the graph holds since the capture (ssd_buffer_epoch)."""
+        if not self.ctx._h or any(not r._h for r in self.routers) or \
+                (self.global_sketch is not None and not self.global_sketch._h):
+            raise RuntimeError("the context or a sketch of this graph has been closed")
         if int(self.ctx.L.ssd_buffer_epoch(self.ctx._h)) != self._epoch:
             raise RuntimeError("the context replaced buffers this graph holds (a new touch chunk size, "
                                "ssd_reserve or a larger slot); capture the slot again")
