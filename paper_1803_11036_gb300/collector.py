@@ -64,8 +64,9 @@ class SlotCollector:
 
     # ---- submissions
     def submit(self, router: int, slot: int, pairs) -> str:
-        """Hand over router's slice of `slot`. Returns "accepted", "held" (a later slot), "late"
-        or "duplicate"."""
+        """Hand over router's slice of `slot`: a device tensor of (cip, oip) pairs, as for
+        Context.slot (it is read when the slot closes). Returns "accepted", "held" (a later slot),
+        "late" or "duplicate"."""
         if not 0 <= router < len(self.routers):
             raise ValueError(f"no router {router}")
         if self._opened is None:
