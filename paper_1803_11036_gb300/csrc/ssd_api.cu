@@ -870,7 +870,8 @@ int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs) {
     }
     ctx->packed_cap = max_pairs;
   }
-  const uint64_t bytes = ((max_pairs * 8 + 15) & ~15ull) + 256;
+  // ssd_slot_host starts each router's pairs on a 16-byte boundary: up to 15 bytes per router more
+  const uint64_t bytes = ((max_pairs * 8 + 15) & ~15ull) + 16ull * SSD_MAX_ROUTERS + 256;
   if (bytes > ctx->hs_bytes) {
     ctx->epoch += 1;
     for (int i = 0; i < 2; ++i) {
