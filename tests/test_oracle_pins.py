@@ -529,3 +529,37 @@ def test_literal_shift_regain_forms_agree(name, nslots):
             assert all(oracle.rk_row(p, gsk, i)[cols[i]] >= thr for i in range(p.r))
         listed += len(b["ips"])
     assert listed > 0
+
+
+@pytest.mark.parametrize("name", ["paper_c1", "edge_small"])
+def test_sampled_estimators_follow_the_full_sketch(name):
+    """oracle.Sampled (Algorithm 2 and the recorder update restricted to chosen estimators, the
+    oracle of the full-size tests) equals the full RSEA of the oracle's pipeline on every chosen
+    estimator of every router after every slot: two separate routines (a hashed subset against the
+    whole array) agree."""
+    W = tg.workload(name)
+    p = oracle.params(W["params"])
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    rng = np.random.default_rng(3)
+    hosts = T.planted_ips()[:5].tolist()
+    rows = [i for _ in hosts for i in range(p.r)] + rng.integers(0, p.r, 60).tolist()
+    cols = [int(c) for x in hosts for c in oracle.rhfg(p, tabs, x)] + rng.integers(0, p.C, 60).tolist()
+    rows = np.array(rows, dtype=np.uint32)
+    cols = np.array(cols, dtype=np.uint32)
+    pipe = oracle.Pipeline(p, tabs, T.routers)
+    samp = [oracle.Sampled(p, rows, cols) for _ in range(T.routers)]
+    touched = 0
+    for t in range(4):
+        pairs = T.slot(t)
+        pipe.step(pairs, regain_method=None)
+        for j in range(T.routers):
+            if t:
+                samp[j].advance()
+            samp[j].scan(tabs, pairs[j])
+            full = pipe.routers[j].reshape(p.r, p.C, p.eta)
+            for r_, c_ in zip(rows.tolist(), cols.tolist()):
+                got = samp[j].get(r_, c_)
+                assert np.array_equal(got, full[r_, c_]), (t, j, r_, c_)
+                touched += int((got < p.k).sum())
+    assert touched > 0
