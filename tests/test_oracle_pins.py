@@ -563,3 +563,18 @@ def test_sampled_estimators_follow_the_full_sketch(name):
                 assert np.array_equal(got, full[r_, c_]), (t, j, r_, c_)
                 touched += int((got < p.k).sum())
     assert touched > 0
+
+
+def test_oracle_lists_match_the_committed_fixture():
+    """The oracle's lists, R_k, level counts and staged tuples for two seeded workloads equal those
+    written by tests/golden/make_oracle_lists.py when the fixture was made: a change to the oracle's
+    arithmetic shows here and must come with a regenerated fixture."""
+    import json
+    import importlib.util
+    here = os.path.join(ROOT, "tests", "golden")
+    spec = importlib.util.spec_from_file_location("make_oracle_lists", os.path.join(here, "make_oracle_lists.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "oracle_lists.json")) as f:
+        want = json.load(f)
+    assert mod.compute() == want
