@@ -9,7 +9,12 @@
  *   literal mode: x is listed iff for SOME column h of row 0 the tuple
  *                 (h, h^B(1)(x), ..., h^B(r-1)(x)) is all hot with union
  *                 R_k >= threshold, where B(i)(x) is the q-bit window of x
- *                 starting at bit (i-1)*delta; R_k is the largest such.
+ *                 starting at bit (i-1)*delta + sh0; R_k is the largest such.
+ *
+ * sh0 = 0 is the shift the library adopts, (i-1)*delta; sh0 = delta is Eq. 2 as
+ * printed, i*delta. Under the printed shift no window holds bits 0..delta-1,
+ * and a host is regained when its own tuple (verify mode) passes: the windows
+ * fix bits delta..31 and RHFG[0](x) = h fixes the rest.
  *
  * Both follow from Eq. 2-3 and the final test of Algorithm 4. Test helper only.
  */
@@ -22,6 +27,7 @@ typedef struct {
   const uint32_t* tables;   /* 2048 words */
   const uint8_t* hot;       /* r * 2^q flags */
   const uint32_t* bitmaps;  /* r * 2^q * (eta/32) words: bit j set iff recorder j < k */
+  uint32_t sh0;             /* shift of window B(1): 0, or delta for Eq. 2 as printed */
 } bf_in;
 
 static uint32_t fwd_hash(const uint32_t* T, uint32_t x) {
@@ -29,7 +35,7 @@ static uint32_t fwd_hash(const uint32_t* T, uint32_t x) {
 }
 
 static uint32_t window(const bf_in* in, uint32_t x, uint32_t i) {
-  uint32_t s = (i - 1) * in->delta;
+  uint32_t s = (i - 1) * in->delta + in->sh0;
   uint32_t v = s < 32 ? x >> s : 0;
   return v & ((1u << in->q) - 1);
 }

@@ -320,11 +320,13 @@ def _bruteforce_lib():
 
 class _BfIn(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("log2_eta", "q", "r", "delta", "k", "thr")] + \
-               [("tables", ctypes.c_void_p), ("hot", ctypes.c_void_p), ("bitmaps", ctypes.c_void_p)]
+               [("tables", ctypes.c_void_p), ("hot", ctypes.c_void_p), ("bitmaps", ctypes.c_void_p),
+                ("sh0", ctypes.c_uint32)]
 
 
-def bruteforce(p, tabs, sk, verify):
-    """All hosts in [0, 2^32) the definitions list, computed forward (see brute_force.c)."""
+def bruteforce(p, tabs, sk, verify, sh0=0):
+    """All hosts in [0, 2^32) the definitions list, computed forward (see brute_force.c). sh0 is
+    the bit where window B(1) starts: 0 for the (i-1)*delta windows, delta for Eq. 2 as printed."""
     thr, _ = oracle.threshold(p.eta, p.theta)
     below = (sk.reshape(p.r, p.C, p.eta) < p.k)
     rk = below.sum(axis=2)
@@ -336,7 +338,7 @@ def bruteforce(p, tabs, sk, verify):
     cap = 1 << 20
     xs = np.empty(cap, np.uint32)
     rks = np.empty(cap, np.uint32)
-    bi = _BfIn(p.log2_eta, p.q, p.r, p.delta, p.k, thr, tabs.ctypes.data, hot.ctypes.data, bm.ctypes.data)
+    bi = _BfIn(p.log2_eta, p.q, p.r, p.delta, p.k, thr, tabs.ctypes.data, hot.ctypes.data, bm.ctypes.data, sh0)
     n = _bruteforce_lib().bf_enumerate(ctypes.byref(bi), int(verify), ctypes.c_void_p(h0.ctypes.data),
                                        ctypes.c_uint32(h0.size), ctypes.c_void_p(xs.ctypes.data),
                                        ctypes.c_void_p(rks.ctypes.data), ctypes.c_uint64(cap))
@@ -371,6 +373,29 @@ def test_regain_equals_bruteforce_over_all_ipv4():
             assert np.array_equal(got["ips"], bx)
             assert np.array_equal(got["rk"], brk)
             assert len(bx) > 0
+
+
+@pytest.mark.slow
+def test_literal_shift_regain_equals_bruteforce_over_all_ipv4():
+    """Completeness of Eq. 2 as printed (windows at i*delta): the sketch is scanned with the
+    printed shift, and over every IPv4 value the regained list equals the forward definition -
+    x is listed iff its own r estimators RHFG[i](x) are hot with union R_k >= threshold. A
+    completion of bits 0..delta-1 that the regain wrongly dropped, or a host it made up, fails
+    here; the soundness pins alone would pass both."""
+    for W in (tg.workload("tiny"), _dense_tiny()):
+        p = oracle.params(W["params"], oracle.RHFG_LITERAL)
+        tabs = tg.hash_tables(W["hash_seed"])
+        T = tg.Traffic(**W["traffic"])
+        pipe = oracle.Pipeline(p, tabs, T.routers)
+        total = 0
+        for ts in range(4):
+            pipe.step(T.slot(ts), regain_method=None)
+            got = oracle.regain(p, tabs, pipe.global_sk, "levelwise")
+            bx, brk = bruteforce(p, tabs, pipe.global_sk, True, sh0=p.delta)
+            assert np.array_equal(got["ips"], bx), ts
+            assert np.array_equal(got["rk"], brk), ts
+            total += len(bx)
+        assert total > 0
 
 
 # ---------------------------------------------------------- precise algorithm
