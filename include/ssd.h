@@ -242,19 +242,24 @@ SSD_API int ssd_regain(ssd_ctx* ctx, const ssd_sketch* global, uint32_t* d_ips, 
  * counterpart; this is a deployment variant of the same computation.)
  *   p: the parameter set (its capacity fields are ignored: the array decides
  *      them, at most 4096 hot estimators per row);
+ *   side, group_bits, group: the view of the sketch the recorders come from
+ *      (ssd_sketch_view; checked as ssd_sketch_set_view checks them). With
+ *      group_bits > 0 the list holds only hosts of `group`, as in ssd_regain;
  *   d_tables: the 2048 hash-table words of ssd_create, in device memory;
  *   d_recorders: a whole RSEA (ssd_sketch_bytes bytes, 16-byte aligned) in
  *      device memory on the current device;
  *   d_ips, d_rk, cap, *n_out: as in ssd_regain.
- * Runs on the caller's current device and waits for `stream`. The first call
- * on a device looks up the array's device address (once per device); make that
- * first call before any stream capture. Returns SSD_ECAPACITY when the
- * parameter set needs more scratch than the array holds (r * 2^q four-byte
- * entries must stay under 16 MiB: q <= 19 at r = 5) or when a capacity overflowed. Every
- * call shares the one array and leaves its contents behind; calls that overlap
- * on the GPU race and must be serialised by the caller. */
-SSD_API int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, const uint16_t* d_recorders,
-                              uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* n_out, void* stream);
+ * Runs on the caller's current device. Every call looks up the array's device
+ * address on that device (cudaGetSymbolAddress) and waits for `stream` before
+ * returning (synchronous). Returns SSD_ECAPACITY when the parameter set needs
+ * more scratch than the array holds (r * 2^q four-byte entries must stay under
+ * 16 MiB: q <= 19 at r = 5) or when a capacity overflowed. Every call shares
+ * the one array and leaves its contents behind (the counters are cleared at
+ * the start of each call); calls that overlap on the GPU race and must be
+ * serialised by the caller. */
+SSD_API int ssd_regain_static(const ssd_params* p, uint32_t side, uint32_t group_bits, uint32_t group,
+                              const uint32_t* d_tables, const uint16_t* d_recorders, uint32_t* d_ips,
+                              uint32_t* d_rk, uint64_t cap, uint64_t* n_out, void* stream);
 
 /* End of slot for n routers, fully asynchronous and free of host
  * synchronisation (it can be captured in a CUDA graph): one streaming pass

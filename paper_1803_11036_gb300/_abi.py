@@ -72,7 +72,7 @@ SIGNATURES = {
     "ssd_advance": ([_vp, _int, _vp], _int),
     "ssd_merge": ([_vp, _int, _vp, _vp], _int),
     "ssd_regain": ([_vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
-    "ssd_regain_static": ([_PP, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
+    "ssd_regain_static": ([_PP, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_close_slot": ([_vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_slot": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),
     "ssd_slot_host": ([_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),

@@ -232,7 +232,7 @@ void free_ctx(ssd_ctx* c) {
 
 extern "C" {
 
-int ssd_version(void) { return 102; }
+int ssd_version(void) { return 103; }
 
 const char* ssd_strerror(int code) {
   switch (code) {

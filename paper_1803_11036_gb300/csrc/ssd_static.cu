@@ -8,8 +8,6 @@
 // that must not pay cudaMalloc's implicit device synchronisation. They pass the
 // parameter set, the hash tables and the recorders already in device memory,
 // and the output buffers; nothing else is needed.
-#include <mutex>
-
 #include "ssd_internal.cuh"
 
 namespace {
@@ -19,23 +17,18 @@ namespace {
 constexpr uint64_t kStaticBytes = 32ull << 20;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_static_addr[kMaxDevices] = {};
-std::mutex g_static_mu;
-
-// Device address of g_static_scratch on the current device. In host code the
-// array's name is only a host-side stand-in; the address must come from
-// cudaGetSymbolAddress with that device current (done once per device).
-int static_address(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxDevices) return SSD_EINVAL;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) return SSD_ECUDA;
-    g_static_addr[dev] = p;
+// Device address of g_static_scratch on the caller's current device. In host code the array's
+// name is only a host-side stand-in; the address comes from cudaGetSymbolAddress with that device
+// current. It is looked up on every call, not cached: after cudaDeviceReset (or any new primary
+// context) the module is loaded again and an address kept from before would be stale.
+int static_address(void** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return SSD_ECUDA;
   }
-  *out = g_static_addr[dev];
+  *out = p;
   return SSD_OK;
 }
 
@@ -76,9 +69,13 @@ int plan_for(ssd::Dims& d, Plan& pl) {
 
 }  // namespace
 
-extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, const uint16_t* d_recorders,
-                                 uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* n_out, void* stream) {
+extern "C" int ssd_regain_static(const ssd_params* p, uint32_t side, uint32_t group_bits, uint32_t group,
+                                 const uint32_t* d_tables, const uint16_t* d_recorders, uint32_t* d_ips,
+                                 uint32_t* d_rk, uint64_t cap, uint64_t* n_out, void* stream) {
   if (!p || !d_tables || !d_recorders || !n_out || (cap && (!d_ips || !d_rk))) return SSD_EINVAL;
+  // the view of the sketch the recorders come from, checked as ssd_sketch_set_view checks it
+  if (side > SSD_SIDE_ONET || group_bits > SSD_MAX_GROUP_BITS || (group >> group_bits)) return SSD_EINVAL;
+  const uint32_t view = ssd::view_pack(side, group_bits, group);
   if (reinterpret_cast<uintptr_t>(d_recorders) & 15u) return SSD_EINVAL;
   if (ssd_params_check(p) != SSD_OK) return SSD_EINVAL;
   int dev = -1;
@@ -96,7 +93,7 @@ extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, 
   int rc = plan_for(d, pl);
   if (rc != SSD_OK) return rc;
   void* base = nullptr;
-  rc = static_address(dev, &base);  // first call on a device: the set-up
+  rc = static_address(&base);
   if (rc != SSD_OK) return rc;
   unsigned char* b = static_cast<unsigned char*>(base);
   ssd::Scratch s;
@@ -123,7 +120,8 @@ extern "C" int ssd_regain_static(const ssd_params* p, const uint32_t* d_tables, 
   a.global = nullptr;
   if (ssd::launch_stream(d, s, a, ssd::kHot, sms, ssd::default_tuning(), st) != cudaSuccess) return SSD_ECUDA;
   int launches = 0;
-  if (ssd::launch_regain_tail(d, s, d_ips, d_rk, cap, nd, sms, st, &launches) != cudaSuccess) return SSD_ECUDA;
+  if (ssd::launch_regain_tail(d, s, d_ips, d_rk, cap, nd, sms, st, &launches, view) != cudaSuccess)
+    return SSD_ECUDA;
   ssd::DevCounters h;
   if (cudaMemcpyAsync(&h, s.counters, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SSD_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SSD_ECUDA;

@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert set(names) == set(_abi.SIGNATURES), set(names) ^ set(_abi.SIGNATURES)
-    assert L.ssd_version() == 102
+    assert L.ssd_version() == 103
 
 
 def test_only_the_abi_is_exported():

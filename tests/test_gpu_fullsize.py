@@ -1,12 +1,22 @@
-"""Parity at the full size of the benchmark workload (one core-link router, 6.25 M packets per
-slot, q = 18, a 5 GiB RSEA), in the launch configuration bench.py times: ssd_scan then
-ssd_close_slot with no global sketch, every slot.
+"""Exact parity at the full size of the benchmark workload, on the route bench.py times.
 
-The full RSEA is too large for the oracle to hold and advance slot by slot, so the oracle follows
-a sample of estimators through every packet (Algorithm 2 and the recorder update restricted to
-them) and decides, for a sample of hosts, whether each is a sliding super point. With the RHFG[0]
-check on, a host is in the list exactly when all r of its estimators RHFG[i](x) are hot and the
-union of the r has R_k >= the threshold, which the sampled estimators decide completely."""
+Workload: one core-link router, 6.25 M packets per slot, eta = 2^11, q = 18, r = 5 (a 5 GiB RSEA),
+k = 60, theta = 1024, run for k + 4 slots so the window rolls over.
+
+Route A is bench.py's timed step: one ssd_slot call per slot with flags 0 (Algorithm 4's final
+test without the RHFG[0] check, as the paper prints it), no global sketch, and the default launch
+configuration, which ssd_autotune keeps on this workload. In that call the pairs are pre-hashed once,
+one launch collects chunk 0's touch bits, and ten chunk launches run as programmatic dependents,
+each applying its chunk's bits and collecting the next chunk's.
+
+Route B is the same traffic through ssd_scan + ssd_close_slot with the RHFG[0] check and the merged
+sketch written every slot.
+
+The oracle holds the whole RSEA in host memory and runs Algorithm 2 and the distance recorder
+update on every slot. The checks are exact, not sampled:
+- both lists and their R_k, entry by entry, at slots inside and after the first window;
+- a block of recorders of every router and of the merged sketch at every slot;
+- every recorder of both routers and of the merged sketch after the last slot."""
 import numpy as np
 import pytest
 
@@ -17,71 +27,76 @@ from gpu_harness import to_dev
 
 pytestmark = pytest.mark.gpu
 
-SLOTS = 24
+BLOCK = 1 << 22   # recorders compared at every slot (8 MiB, at a slot-dependent offset)
 
 
-def test_corelink_full_size_sampled():
+def _assert_list(got, want, where):
+    gi, gr = got
+    assert len(gi) == len(want["ips"]), f"{where}: {len(gi)} hosts, oracle {len(want['ips'])}"
+    assert np.array_equal(gi, want["ips"]), f"{where}: hosts differ"
+    assert np.array_equal(gr, want["rk"]), f"{where}: R_k differs"
+
+
+def test_corelink_full_size_bench_route_exact():
     import torch
     W = tg.workload("corelink_c2")
     prm = W["params"]
+    k = prm["k"]
+    slots = k + 4
+    checkpoints = {9, k - 1, k, slots - 1}
     tabs = tg.hash_tables(W["hash_seed"])
     T = tg.traffic_for(W)
-    # A: the bench configuration (literal regain, routers only); B: the same traffic with the
-    # RHFG[0] check and the merged sketch written every slot.
+    assert T.routers == 1
+
     ctx_a = ssd.Context(ssd.make_params(prm), tabs)
     ctx_b = ssd.Context(ssd.make_params(prm, ssd.SSD_VERIFY_H0), tabs)
     ra, rb, gb = ctx_a.sketch(), ctx_b.sketch(), ctx_b.sketch()
-    slots = T.fill_many([(t, 0) for t in range(SLOTS)])
-    la = lb = None
-    for t in range(SLOTS):
-        dev = to_dev(slots[t])
-        ctx_a.scan(ra, dev)
-        la = ctx_a.close_slot([ra])
-        ctx_b.scan(rb, dev)
-        lb = ctx_b.close_slot([rb], gb)
-        del dev
-    torch.cuda.synchronize()
-    # the two configurations hold the same routers, and the checked list is inside the literal one
     n_rec = ctx_a.sketch_bytes // 2
-    for off in range(0, n_rec, 1 << 28):
-        c = min(1 << 28, n_rec - off)
-        assert np.array_equal(ra.export(off, c), rb.export(off, c)), off
-    assert set(lb[0].tolist()) <= set(la[0].tolist())
-    assert len(lb[0]) > 10
-
-    p = oracle.params(prm, oracle.VERIFY_H0)
-    thr, _ = oracle.threshold(p.eta, p.theta)
-    rng = np.random.default_rng(5)
-    hosts = set(T.planted_ips().tolist()) | set(lb[0].tolist()) | set(la[0][:50].tolist())
-    hosts |= {T.lib.tg_src_ip(T._h, int(s)) for s in rng.integers(0, W["traffic"]["n_src"], 200)}
-    hosts = sorted(hosts)
-    cols = {x: oracle.rhfg(p, tabs, x) for x in hosts}
-    rows = np.concatenate([np.arange(p.r, dtype=np.uint32) for _ in hosts])
-    cc = np.concatenate([cols[x] for x in hosts]).astype(np.uint32)
-    extra_c = rng.integers(0, p.C, 64).astype(np.uint32)
-    extra_r = rng.integers(0, p.r, 64).astype(np.uint32)
-    sampled = oracle.Sampled(p, np.concatenate([rows, extra_r]), np.concatenate([cc, extra_c]))
-    for t in range(SLOTS):
+    p_lit = oracle.params(prm)
+    p_chk = oracle.params(prm, oracle.VERIFY_H0)
+    sk = oracle.new_sketch(p_lit)
+    assert sk.size == n_rec
+    rng = np.random.default_rng(7)
+    listed = {"literal": 0, "checked": 0}
+    for t in range(slots):
+        pairs = T.slot(t)[0]
+        # oracle: advance at the start of every slot after the first, then Algorithm 2
         if t:
-            sampled.advance()
-        sampled.scan(tabs, slots[t])
-    # state after the last slot's close = one more advance
-    sampled.advance()
-    for row, col in list(zip(extra_r.tolist(), extra_c.tolist())) + [(i, int(cols[hosts[0]][i])) for i in range(p.r)]:
-        assert np.array_equal(ra.export_estimator(row, col), sampled.get(row, col)), (row, col)
-    # membership and R_k of every sampled host in the checked list (pre-advance recorders:
-    # recorder < k before the advance is recorder < k + 1 after it, with 65535 staying 65535)
-    got = dict(zip(lb[0].tolist(), lb[1].tolist()))
-    checked_in = 0
-    for x in hosts:
-        below = [sampled.get(i, int(cols[x][i])) < p.k + 1 for i in range(p.r)]
-        rks = [int(b.sum()) for b in below]
-        union = int(np.logical_and.reduce(below).sum())
-        member = all(v >= thr for v in rks) and union >= thr
-        assert (x in got) == member, hex(x)
-        if member:
-            assert got[x] == union, hex(x)
-            checked_in += 1
-    assert checked_in == len(lb[0])   # every listed host was sampled and confirmed
+            oracle.advance(p_lit, sk)
+            # both routers after slot t-1's close hold the advanced recorders
+            off = int(rng.integers(0, n_rec - BLOCK))
+            assert np.array_equal(ra.export(off, BLOCK), sk[off:off + BLOCK]), (t, off)
+            assert np.array_equal(rb.export(off, BLOCK), sk[off:off + BLOCK]), (t, off)
+        oracle.scan(p_lit, tabs, sk, pairs)
+        dev = to_dev(pairs)
+        got_a = ctx_a.slot([ra], [dev])
+        ctx_b.scan(rb, dev)
+        got_b = ctx_b.close_slot([rb], gb)
+        del dev
+        # the merged sketch of slot t is the state before the close's advance
+        off = int(rng.integers(0, n_rec - BLOCK))
+        assert np.array_equal(gb.export(off, BLOCK), sk[off:off + BLOCK]), (t, off)
+        if t in checkpoints:
+            want_lit = oracle.regain(p_lit, tabs, sk, "pruned")
+            want_chk = oracle.regain(p_chk, tabs, sk, "pruned")
+            _assert_list(got_a, want_lit, f"slot {t}, ssd_slot, literal list")
+            _assert_list(got_b, want_chk, f"slot {t}, ssd_close_slot, checked list")
+            assert ctx_b.stats()["hot"] == [int(oracle.hse(p_chk, sk, i).size) for i in range(p_chk.r)]
+            listed["literal"] += len(want_lit["ips"])
+            listed["checked"] += len(want_chk["ips"])
+    torch.cuda.synchronize()
+    assert listed["checked"] > 10 and listed["literal"] >= listed["checked"]
+
+    # every recorder: the merged sketch of the last slot, then both routers one advance further
+    step = 1 << 28
+    for off in range(0, n_rec, step):
+        c = min(step, n_rec - off)
+        assert np.array_equal(gb.export(off, c), sk[off:off + c]), ("global", off)
+    oracle.advance(p_lit, sk)
+    for off in range(0, n_rec, step):
+        c = min(step, n_rec - off)
+        assert np.array_equal(ra.export(off, c), sk[off:off + c]), ("ssd_slot router", off)
+        assert np.array_equal(rb.export(off, c), sk[off:off + c]), ("ssd_close_slot router", off)
+    assert ra.slot == rb.slot == slots
     ctx_a.close()
     ctx_b.close()
