@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-stress", action="store_true", help="skip the 32-router batched-vs-plain leg")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-c1", action="store_true", help="skip the leg at the paper's own dimensions")
     ap.add_argument("--touch-chunk-mib", type=int, default=0, help="touch bits per chunk of the fused slot")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     return ap.parse_args()
@@ -229,6 +230,68 @@ def gbps(mpps: float):
             "paper_convention": round(mpps * PAPER_PACKET_BYTES * 8 / 1024, 2)}
 
 
+def traced(ctx, stream, calls):
+    """Run each call (one slot, or one slot close) with trace events at its phase boundaries;
+    returns the per-call milliseconds of the streaming pass (start -> pass) and of the candidate
+    levels and list (pass -> end)."""
+    import torch
+    E = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in calls]
+    with torch.cuda.stream(stream):
+        for e, call in zip(E, calls):
+            for ev in e:
+                ev.record(stream)   # torch marks them recorded; the library re-records them in place
+            ctx.set_trace(e[0], e[1], e[2])
+            call()
+    stream.synchronize()
+    ctx.set_trace()
+    return [e[0].elapsed_time(e[1]) for e in E], [e[1].elapsed_time(e[2]) for e in E]
+
+
+def step_rooflines(pk, scan_ms, scan_pk, slot_pass, slot_tail, close_pass, close_tail, pass_bytes, r, peak):
+    """Each step of the slot against its own roofline (algorithmic bytes / time / measured HBM).
+    scan: 8 B pair read + r x 2 B recorder writes per packet; streaming passes: 4 B per recorder
+    (2 read + 2 written) per router; the candidate levels and the list are latency-bound (a few
+    MB of bitmaps in L2 per slot), so only their time is given."""
+    scan_b = 8 + 2 * r
+    sp, cp = statistics.mean(slot_pass), statistics.mean(close_pass)
+    marginal = sp - cp
+    def frac(b, ms):
+        return None if ms <= 0 else round(b / (ms / 1e3) / 1e9 / peak, 4)
+    def gbs(b, ms):
+        return None if ms <= 0 else round(b / (ms / 1e3) / 1e9, 1)
+    return {
+        "scan_standalone": {
+            "what": "ssd_scan_batch alone: Algorithm 2 storing r recorders per packet directly",
+            "ms_per_slice": round(scan_ms, 4), "gpps": round(scan_pk / scan_ms / 1e6, 2),
+            "algorithmic_bytes_per_packet": scan_b, "achieved_gbs": gbs(scan_b * scan_pk, scan_ms),
+            "bound": "hbm (random 32 B sector read-modify-writes)", "frac": frac(scan_b * scan_pk, scan_ms)},
+        "scan_in_slot": {
+            "what": "the scan's marginal cost inside ssd_slot: streaming pass with the scan's touches "
+                    "minus the close-only pass, same slices",
+            "ms_per_slice": round(marginal, 4), "gpps": round(pk / marginal / 1e6, 2) if marginal > 0 else None,
+            "algorithmic_bytes_per_packet": scan_b, "achieved_gbs": gbs(scan_b * pk, marginal),
+            "bound": "l2 atomics (touch bits)", "frac": frac(scan_b * pk, marginal),
+            "target_frac": 0.5, "target_met": bool(marginal > 0 and scan_b * pk / (marginal / 1e3) / 1e9 >= 0.5 * peak)},
+        "slot_pass": {
+            "what": "streaming pass of ssd_slot with the scan inside (pre-hash, chunk 0's touches, chunk "
+                    "launches: touches applied, hot extraction, advance, next chunk's touches)",
+            "ms_per_slice": round(sp, 4), "algorithmic_bytes": pass_bytes, "achieved_gbs": gbs(pass_bytes, sp),
+            "bound": "hbm", "frac": frac(pass_bytes, sp)},
+        "close_pass": {
+            "what": "ssd_close_slot's streaming pass with no scan (merge, hot extraction, advance: one launch)",
+            "ms_per_slice": round(cp, 4), "algorithmic_bytes": pass_bytes, "achieved_gbs": gbs(pass_bytes, cp),
+            "bound": "hbm", "frac": frac(pass_bytes, cp)},
+        "regain_tail": {
+            "what": "pair level, row levels, final test and the sorted list (five launches)",
+            "ms_per_slice": round(statistics.mean(slot_tail), 4),
+            "ms_per_slice_after_close_only": round(statistics.mean(close_tail), 4),
+            "bound": "latency (a few MB of bitmaps in L2; SMs mostly idle)"},
+        "peak_gbs": peak,
+        "measured": "CUDA events on the launching stream (ssd_set_trace) over 10 slots run right after the "
+                    "timed region on the same slices, then 10 closes with no scan",
+    }
+
+
 # ---------------------------------------------------------- CPU oracle leg
 
 def oracle_sample(W: dict):
@@ -388,6 +451,81 @@ def batched_vs_plain(rank: int, local: int, name: str = "edge16_c3", fill: int =
             "note": "plain = per-router scans + merge + regain + advance; batched = one scan launch + fused close"}
 
 
+def paper_c1_leg(rank: int, local: int, warmup: int = 3, steps: int = 30) -> dict:
+    """The paper's own dimensions (Sec. 5: eta = 2^11, q = 14, r = 5, delta = 6, theta = 1024; a
+    320 MiB RSEA, 2.5x L2) with one router, 2^18 packets per slot and a window of 4 slots, through
+    the bench's step (ssd_slot, default configuration): the window is filled first, then `steps`
+    slots are timed with nothing else on the stream; the split into steps comes from a traced
+    repeat of the first ten."""
+    import torch
+
+    import paper_1803_11036_gb300 as ssd
+    import trafficgen as tg
+
+    dev = torch.device("cuda", local)
+    W = replica_workload("paper_c1", rank)
+    prm = W["params"]
+    T = tg.Traffic(**W["traffic"])
+    fill = prm["k"]
+    n = fill + warmup + steps
+    slots = [torch.from_numpy(v.reshape(-1).view(np.int32)).to(dev) for v in T.fill_many([(t, 0) for t in range(n)])]
+    pk = [x.numel() // 2 for x in slots]
+    ctx = ssd.Context(ssd.make_params(prm), tg.hash_tables(W["hash_seed"]), device=local)
+    router = ctx.sketch()
+    cap = 1 << 16
+    out = (torch.empty(cap, dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev),
+           torch.zeros(1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.Stream(dev)
+
+    def step(t):
+        ctx.slot([router], [slots[t]], None, out=out, stream=stream, sync=False)
+
+    with torch.cuda.stream(stream):
+        for t in range(fill + warmup):
+            step(t)
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for t in range(fill + warmup, n):
+            step(t)
+        b.record(stream)
+    stream.synchronize()
+    launches = (ctx.launch_count - l0) / steps
+    st = ctx.stats(stream)
+    ms = a.elapsed_time(b) / steps
+    timed = sum(pk[fill + warmup:])
+    tr = list(range(fill + warmup, fill + warmup + min(10, steps)))
+    slot_pass, slot_tail = traced(ctx, stream, [lambda t=t: step(t) for t in tr])
+    close_pass, close_tail = traced(ctx, stream, [lambda: ctx.close_slot([router], None, out=out, stream=stream,
+                                                                         sync=False)] * len(tr))
+    eta, C, r = 1 << prm["log2_eta"], 1 << prm["q"], prm["r"]
+    peak, _ = measured_peak()
+    scratch = ctx.sketch()
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ctx.scan(scratch, slots[fill], stream=stream)
+        sa.record(stream)
+        for t in tr:
+            ctx.scan(scratch, slots[t], stream=stream)
+        sb.record(stream)
+    stream.synchronize()
+    scan_ms = sa.elapsed_time(sb) / len(tr)
+    steps_ = step_rooflines(pk=statistics.mean(pk[t] for t in tr), scan_ms=scan_ms,
+                            scan_pk=statistics.mean(pk[t] for t in tr), slot_pass=slot_pass, slot_tail=slot_tail,
+                            close_pass=close_pass, close_tail=close_tail, pass_bytes=eta * C * r * 4, r=r, peak=peak)
+    ctx.close()
+    torch.cuda.empty_cache()
+    mpps = timed / (ms * steps / 1e3) / 1e6
+    return {"workload": "paper_c1", "routers": 1, "packets_per_slot": pk[-1], "k": prm["k"], "eta": eta,
+            "q": prm["q"], "r": r, "delta": prm["delta"], "theta": prm["theta"], "window_filled_slots": fill,
+            "steps": steps, "ms_per_slot": round(ms, 4), "mpps": round(mpps, 1), "gbps_at_800B": gbps(mpps),
+            "launches_per_slot": launches, "list_size": st["n_out"], "hot_per_row": st["hot"],
+            "split": steps_,
+            "l2": "the 320 MiB RSEA (2.5x L2) is streamed every slot and each slot scans a distinct slice"}
+
+
 def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64, per_router: int = 4,
                offered_per_s: float = 500.0, max_inflight: int = 16, tuning: dict | None = None) -> dict:
     """Routers stream slices at Poisson times; each slice is scanned and closed on its router's
@@ -490,8 +628,7 @@ def run_ours(args, world, rank, local):
     if st_fill["status"]:
         raise RuntimeError(f"capacity status {st_fill['status']} during fill")
 
-    # ---- timed region
-    E = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # ---- timed region: K slots, nothing but the slot calls on the stream
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = ctx.launch_count
     clocks = Clocks(local)
@@ -501,29 +638,32 @@ def run_ours(args, world, rank, local):
     with torch.cuda.stream(stream):
         t_start.record(stream)
         for i in range(args.steps):
-            e = E[i]
-            for ev in e:
-                ev.record(stream)   # torch marks them recorded; the library re-records them in place
-            ctx.set_trace(e[0], e[1], e[2])
             step(fill + args.warmup + i)
         t_end.record(stream)
     stream.synchronize()
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
-    ctx.set_trace()
     launches = ctx.launch_count - launches0
     st = ctx.stats(stream)
     if st["status"]:
         raise RuntimeError(f"capacity status {st['status']} in the timed region")
 
     total_ms = t_start.elapsed_time(t_end)
-    pass_ms = [E[i][0].elapsed_time(E[i][1]) for i in range(args.steps)]
-    tail_ms = [E[i][1].elapsed_time(E[i][2]) for i in range(args.steps)]
     timed_pk = sum(pk_per_slot[fill + args.warmup:])
     max_ms = max_over_ranks(total_ms, world)
     all_pk = sum_over_ranks(timed_pk, world)
     value = all_pk / (max_ms / 1e3) / 1e6
+
+    # ---- the split of a slot into its steps, outside the timed region: the first timed slices
+    # again, with trace events at the phase boundaries (ssd_set_trace), then the same number of
+    # slot closes with no scan (ssd_close_slot: the streaming pass without touch bits)
+    n_tr = min(args.steps, 10)
+    tr_slots = [fill + args.warmup + i for i in range(n_tr)]
+    slot_pass, slot_tail = traced(ctx, stream, [lambda t=t: step(t) for t in tr_slots])
+    close_pass, close_tail = traced(ctx, stream, [lambda: ctx.close_slot(routers, None, out=(ips, rks, n_out),
+                                                                         stream=stream, sync=False)] * n_tr)
+    tr_pk = statistics.mean(pk_per_slot[t] for t in tr_slots)
 
     # ---- realised column load: each row's mean R_k after the last close, through Eq. 1
     occ = routers[0].occupancy(stream)
@@ -595,8 +735,6 @@ def run_ours(args, world, rank, local):
     eta, C, r = 1 << prm["log2_eta"], 1 << prm["q"], prm["r"]
     recorders = eta * C * r
     pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
-    avg_pass_s = statistics.mean(pass_ms) / 1e3
-    achieved = pass_bytes / avg_pass_s / 1e9
     # the pass runs as chunk launches of `chunk` estimators (the tuned touch bits per chunk)
     n_se = r * C
     chunk = 1
@@ -605,7 +743,10 @@ def run_ours(args, world, rank, local):
     n_chunks = -(-n_se // chunk)
     peak, peak_kind = measured_peak()
     traffic = profiled_traffic(args.workload, chunk)
-    scan_alg_bytes = 8 + 2 * r                  # pair read + r recorder writes per packet
+    steps = step_rooflines(pk=tr_pk, scan_ms=scan_ms, scan_pk=timed_pk / args.steps, slot_pass=slot_pass,
+                           slot_tail=slot_tail, close_pass=close_pass, close_tail=close_tail,
+                           pass_bytes=pass_bytes, r=r, peak=peak)
+    achieved = steps["slot_pass"]["achieved_gbs"]
 
     # ---- end to end through the C ABI from pinned host memory: ssd_slot_host copies each
     # slot's pairs to the device (overlapping the previous slot) and the list of every slot
@@ -684,6 +825,7 @@ def run_ours(args, world, rank, local):
     del slot_dev, routers
     ctx.close()
     torch.cuda.empty_cache()
+    c1 = None if args.no_c1 else paper_c1_leg(rank, local)
     bvp = None if args.no_batched else batched_vs_plain(rank, local)
     # 32 routers, 15.6 M packets per slot with ten hot sources (33 RSEAs of 5 GiB); the 300-slot
     # window is not filled, so the regain tail is short and the scan and streaming pass dominate
@@ -707,25 +849,29 @@ def run_ours(args, world, rank, local):
         "default_configuration": default_leg,
         "gbps_at_800B": gbps(value),
         "scan": {"mpps": round(scan_mpps, 2), "gbps_at_800B": gbps(scan_mpps), "ms_per_slice": round(scan_ms, 4),
-                 "achieved_gbs_algorithmic": round(scan_alg_bytes * timed_pk / (scan_ms * args.steps / 1e3) / 1e9, 1),
-                 "note": "ssd_scan alone (recorders written directly); in the timed slot the scan's touches go "
-                         "to L2 bits applied by the streaming pass"},
-        "slot_ms": {"streaming_pass_with_scan": round(statistics.mean(pass_ms), 4),
-                    "candidates_and_list": round(statistics.mean(tail_ms), 4),
+                 "note": "ssd_scan alone (recorders written directly; steps.scan_standalone has its roofline); in "
+                         "the timed slot the scan's touches go to L2 bits applied by the streaming pass "
+                         "(steps.scan_in_slot)"},
+        "slot_ms": {"streaming_pass_with_scan": steps["slot_pass"]["ms_per_slice"],
+                    "candidates_and_list": steps["regain_tail"]["ms_per_slice"],
                     "total": round(max_ms / args.steps, 4)},
-        "reconstruct_ms_per_slice": round(statistics.mean(tail_ms), 4),
+        "reconstruct_ms_per_slice": steps["regain_tail"]["ms_per_slice"],
+        "steps": steps,
+        "paper_c1": c1,
         "cuda_graph": graph_leg,
         "batched_vs_plain": bvp,
         "batched_vs_plain_stress": stress,
         "served": served,
-        "roofline": {"kernel": "k_chunk (one router: the scan's touches applied, hot extraction, advance; the next "
-                               "chunk's touches collected in L2 between estimators), all chunk launches of the pass "
-                               "plus the first chunk's touch launch",
+        "roofline": {"kernel": "the streaming pass of ssd_slot: k_prehash, chunk 0's k_touch_packed and the "
+                               "k_chunk launches (the scan's touches applied, hot extraction, advance; the next "
+                               "chunk's touches collected in L2 between estimators)",
                      "launches_per_pass": n_chunks, "algorithmic_bytes_per_chunk_launch": chunk * eta * 4 * R,
-                     "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": steps["slot_pass"]["frac"], "peak_source": peak_kind,
                      "algorithmic_bytes_per_pass": pass_bytes,
-                     "traffic": traffic},
+                     "traffic": traffic,
+                     "traffic_source": None if traffic is None else
+                     f"profiles/chunk_pass_{args.workload}.md (ncu DRAM bytes of one chunk launch)"},
         "hot_per_row": st["hot"], "candidates_per_level": st["level"], "list_size": st["n_out"],
         "column_load": column_load,
         "gpu_launches": launches,
