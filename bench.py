@@ -208,11 +208,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, chunk: int):
+def profiled_traffic(workload: str, chunk: int, path: str | None = None):
     """DRAM bytes per chunk launch of the streaming pass from the committed ncu summary, if
     the kernel source has not changed since it was captured and the launch covers as many
     estimators as the captured one."""
-    path = os.path.join(ROOT, "profiles", f"chunk_pass_{workload}.md")
+    path = path or os.path.join(ROOT, "profiles", f"chunk_pass_{workload}.md")
     try:
         text = open(path).read()
     except OSError:

@@ -108,6 +108,9 @@ typedef struct ssd_sketch ssd_sketch;
 #define SSD_STATUS_CTB_OVERFLOW 2u  /* more candidate tuples than ctb_capacity */
 #define SSD_STATUS_OUT_OVERFLOW 4u  /* more accepted tuples than out_capacity */
 #define SSD_STATUS_LIST_OVERFLOW 8u /* more hosts than the caller's list capacity */
+#define SSD_STATUS_INTERNAL 16u     /* an internal bound was broken: a library fault, the
+                                       result of the call is not valid (never set by design;
+                                       see also the SSD_DEBUG build) */
 typedef struct ssd_stats {
   uint32_t status;           /* OR of SSD_STATUS_* */
   uint32_t threshold;        /* ceil(R^_k), R^_k = eta * (1 - exp(-theta/eta)) (Sec. 3.3) */
@@ -324,7 +327,7 @@ SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
  * these choices set only how the work of Algorithms 2 and 5 and of the
  * streaming pass (Sec. 4.3) is spread over the GPU. No value changes a
  * recorder, a list or a counter. Defaults: touch_chunk_bytes of the params, 0, 8,
- * 4, 8, 0.
+ * 4, 8, 0, 0.
  *   touch_chunk_bytes: touch bits of one chunk of ssd_slot (64 KiB .. 1 GiB,
  *       rounded up to 256 B; chunk sizes are powers of two that fit it);
  *   stream_blocks_per_sm: resident blocks per SM of the streaming and chunk
@@ -340,7 +343,13 @@ SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
  *       whose bits fall into one word OR them together (__match_any_sync) and
  *       issue one atomic; 2 = the word is read from L2 first and the atomic is
  *       skipped when the bit is already set, which removes the repeats of a
- *       source that sends many packets to few peers. */
+ *       source that sends many packets to few peers;
+ *   collect_touches: where the chunk launches of a one-router ssd_slot find the
+ *       next chunk's touches. 0 = per-chunk touch lists: one launch hashes every
+ *       pair once per slot, sets chunk 0's touch bits and writes the bit index
+ *       of every other touch into its chunk's list (4 bytes per touch), so each
+ *       chunk launch reads only its own touches; 1 = the slot's pairs, hashed
+ *       once into (RHFG[0], H1) words, are re-read by every chunk launch. */
 typedef struct ssd_tuning {
   uint64_t touch_chunk_bytes;
   uint32_t stream_blocks_per_sm;
@@ -348,7 +357,7 @@ typedef struct ssd_tuning {
   uint32_t scan_unroll;
   uint32_t merge_group;
   uint32_t combine_touches;
-  uint32_t reserved; /* must be 0 */
+  uint32_t collect_touches;
 } ssd_tuning;
 
 /* The context's current launch configuration (host only). */

@@ -42,6 +42,10 @@ struct ssd_ctx {
   // pre-hashed pairs of the one-router fused slot (grown to the largest slot)
   uint2* packed;
   uint64_t packed_cap;
+  // per-chunk touch lists of the one-router fused slot (grown to the largest slot) and their counters
+  uint32_t* tl_ent;
+  uint64_t tl_entries;
+  uint32_t* tl_fill;
   // host-pair staging of ssd_slot_host (double-buffered, sized to the largest slot)
   uint32_t* hs_buf[2];
   uint64_t hs_bytes;
@@ -211,6 +215,8 @@ void free_ctx(ssd_ctx* c) {
     cudaFree(c->hs_buf[i]);
   }
   cudaFree(c->packed);
+  cudaFree(c->tl_ent);
+  cudaFree(c->tl_fill);
 
   cudaFree(c->tables);
   cudaFree(c->hot_idx);
@@ -317,6 +323,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
       {(void**)&c->stage, d.out_cap * 8},
       {(void**)&c->counters, sizeof(ssd::DevCounters)},
       {(void**)&c->n_out, 8},
+      {(void**)&c->tl_fill, ssd::kMaxChunks * 4},
       {(void**)&c->bucket_off, NB ? R * (NB + 1) * 4 : 0},
       {(void**)&c->bucket_cnt, NB ? R * NB * 4 : 0},
       {(void**)&c->bucket_ent, NB ? R * d.hse_cap * 4 : 0},
@@ -621,9 +628,58 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   return SSD_OK;
 }
 
-// The fused slot of one router (eta >= 256) in chunks on one stream: chunk 0's
-// touch bits are collected by one launch, then each chunk's streaming kernel
-// applies its bits and, between estimators, collects the next chunk's bits.
+// Entries one touch list of a one-router slot can need: a pair adds at most
+// one touch per row, so a chunk inside one row gets at most n_pairs, a chunk of
+// m whole rows at most m * n_pairs.
+static uint64_t list_cap(const ssd::Dims& d, uint64_t count, uint64_t n_pairs) {
+  uint64_t rows = count >> d.q;
+  if (rows < 1) rows = 1;
+  if (rows > d.r) rows = d.r;
+  return n_pairs * rows;
+}
+
+// Whether the one-router fused slot takes its touches from per-chunk lists: the
+// configuration asks for it and a touch's bit index within its chunk fits 32 bits.
+static bool uses_lists(const ssd_ctx* ctx, uint64_t count) {
+  return ctx->tn.collect == 0 && (count << ctx->d.log2_eta) <= (1ull << 32);
+}
+
+// Grows the touch lists to hold (n_chunks - 1) lists of `cap` entries (waits for the device first).
+static int reserve_lists(ssd_ctx* ctx, uint64_t n_chunks, uint64_t cap) {
+  const uint64_t need = (n_chunks > 1 ? n_chunks - 1 : 0) * cap;
+  if (need <= ctx->tl_entries) return SSD_OK;
+  SSD_CUDA(cudaDeviceSynchronize());
+  cudaFree(ctx->tl_ent);
+  ctx->tl_ent = nullptr;
+  ctx->epoch += 1;
+  const uint64_t want = need + need / 4 + 64;
+  if (cudaMalloc(&ctx->tl_ent, want * 4) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->tl_entries = 0;
+    return SSD_ENOMEM;
+  }
+  ctx->tl_entries = want;
+  return SSD_OK;
+}
+
+// Estimators per chunk of a fused slot of n routers (a power of two: each chunk's
+// touch bits, one per recorder and router, fit the touch buffer) and the chunk count.
+static void chunking(const ssd_ctx* ctx, int n, uint64_t* count, uint64_t* n_chunks) {
+  const ssd::Dims& d = ctx->d;
+  const uint64_t n_se = (uint64_t)d.r << d.q;
+  const uint64_t se_bytes = (uint64_t)n * (d.eta >> 3);  // touch bytes of one estimator, all routers
+  uint64_t c = 1;
+  while (c * 2 * se_bytes <= ctx->touch_bytes && c * 2 <= pow2_at_least(n_se)) c *= 2;
+  *count = c;
+  *n_chunks = (n_se + c - 1) / c;
+}
+
+// The fused slot of one router (eta >= 256) in chunks on one stream. The touches of the
+// slot are found once: by default one launch hashes every pair, sets chunk 0's touch bits
+// and writes the others into per-chunk touch lists; each chunk's streaming kernel applies
+// its bits and, between estimators, sets the next chunk's from its list. Otherwise (the
+// `collect` field of the configuration) the pairs are pre-hashed once and every chunk
+// launch re-reads them all.
 static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs, uint64_t n_pairs,
                         ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk, uint64_t cap, uint64_t* d_n_out,
                         void* stream, uint64_t count, uint64_t n_chunks) {
@@ -639,9 +695,15 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   const uint64_t tgrid = scan_grid(ctx, nvec);
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
+  const bool lists = uses_lists(ctx, count);
+  const uint64_t lcap = list_cap(d, count, n_pairs);
   // both hashes of every pair once per slot when they pack into one word (a grouped view
   // keeps the raw pairs: a pair outside the group must be skippable)
-  const bool prehash = d.q + d.log2_eta <= 32 && ((router->view >> 1) & 31u) == 0;
+  const bool prehash = !lists && d.q + d.log2_eta <= 32 && ((router->view >> 1) & 31u) == 0;
+  if (lists) {
+    rc = reserve_lists(ctx, n_chunks, lcap);   // a larger slot than any before: grow (waits for the device)
+    if (rc != SSD_OK) return rc;
+  }
   if (prehash && n_pairs > ctx->packed_cap) {  // a larger slot than any before: grow (waits for `stream`)
     SSD_CUDA(cudaStreamSynchronize(st));
     cudaFree(ctx->packed);
@@ -665,7 +727,19 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   a.global = global ? global->dr : nullptr;
   a.view = router->view;
   cudaError_t e;
-  if (prehash) {
+  if (lists) {
+    SSD_CUDA(cudaMemsetAsync(ctx->tl_fill, 0, ssd::kMaxChunks * 4, st));
+    ssd::ListArgs la;
+    la.log2_count = 0;
+    while ((1ull << la.log2_count) < count) ++la.log2_count;
+    la.n_chunks = (uint32_t)n_chunks;
+    la.cap = lcap;
+    la.ent = ctx->tl_ent;
+    la.fill = ctx->tl_fill;
+    la.touch0 = ctx->touch[0];
+    la.counters = ctx->counters;
+    e = ssd::launch_lists(d, ctx->tables, b, la, (int)tgrid, ctx->tn, st);
+  } else if (prehash) {
     if (n_pairs) {
       e = ssd::launch_prehash(d, ctx->tables, b, ctx->packed, (int)tgrid, st);
       if (e != cudaSuccess) return cuda_fail(e, "prehash kernel");
@@ -695,9 +769,15 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
       a.next = ctx->touch[(c + 1) & 1];
       a.nx_se0 = (c + 1) * count;
       a.nx_count = n_se - a.nx_se0 < count ? n_se - a.nx_se0 : count;
+      if (lists) {
+        a.list = ctx->tl_ent + c * lcap;        // list of chunk c + 1
+        a.list_fill = ctx->tl_fill + (c + 1);
+      }
     } else {
       a.next = nullptr;
       a.nx_se0 = a.nx_count = 0;
+      a.list = nullptr;
+      a.list_fill = nullptr;
     }
     e = ssd::launch_chunk(d, ctx->s, a, ctx->sms, ctx->tn, st);
     if (e != cudaSuccess) return cuda_fail(e, "chunk kernel");
@@ -733,9 +813,8 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   const ssd::Dims& d = ctx->d;
   const uint64_t n_se = (uint64_t)d.r << d.q;
   const uint64_t se_bytes = (uint64_t)n * (d.eta >> 3);  // touch bytes of one estimator, all routers
-  uint64_t count = 1;
-  while (count * 2 * se_bytes <= ctx->touch_bytes && count * 2 <= pow2_at_least(n_se)) count *= 2;
-  const uint64_t n_chunks = (n_se + count - 1) / count;
+  uint64_t count = 1, n_chunks = 1;
+  chunking(ctx, n, &count, &n_chunks);
   if (n == 1 && d.eta >= 256 && !(d.flags & SSD_SLOT_CHUNKED) && count * se_bytes <= ctx->touch_bytes &&
       count >= 8 && n_chunks <= 32)
     return slot_chunks1(ctx, routers[0], d_pairs[0], n_pairs[0], global, d_ips, d_rk, cap, d_n_out, stream, count,
@@ -859,6 +938,12 @@ int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs) {
   if (!ctx) return SSD_EINVAL;
   DeviceGuard g(ctx->device);
   SSD_CUDA(cudaDeviceSynchronize());
+  uint64_t count = 1, n_chunks = 1;
+  chunking(ctx, 1, &count, &n_chunks);
+  if (uses_lists(ctx, count)) {   // the touch lists of a one-router slot
+    const int rc = reserve_lists(ctx, n_chunks, list_cap(ctx->d, count, max_pairs));
+    if (rc != SSD_OK) return rc;
+  }
   if (max_pairs > ctx->packed_cap) {
     cudaFree(ctx->packed);
     ctx->packed = nullptr;
@@ -920,11 +1005,12 @@ int ssd_tuning_get(const ssd_ctx* ctx, ssd_tuning* out) {
   out->scan_unroll = ctx->tn.unroll;
   out->merge_group = ctx->tn.group;
   out->combine_touches = ctx->tn.combine;
+  out->collect_touches = ctx->tn.collect;
   return SSD_OK;
 }
 
 int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
-  if (!ctx || !t || t->reserved) return SSD_EINVAL;
+  if (!ctx || !t || t->collect_touches > 1) return SSD_EINVAL;
   if (t->touch_chunk_bytes < (64ull << 10) || t->touch_chunk_bytes > (1ull << 30)) return SSD_EINVAL;
   if (t->stream_blocks_per_sm > 8 || t->scan_blocks_per_sm < 1 || t->scan_blocks_per_sm > 32) return SSD_EINVAL;
   const uint32_t u = t->scan_unroll, g = t->merge_group;
@@ -963,6 +1049,7 @@ int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
   ctx->tn.unroll = u;
   ctx->tn.group = g;
   ctx->tn.combine = t->combine_touches;
+  ctx->tn.collect = t->collect_touches;
   return SSD_OK;
 }
 
@@ -1013,7 +1100,7 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
   ssd_tuning best = start;
   int rc = SSD_OK;
   for (int sweep = 0; sweep < 2 && rc == SSD_OK; ++sweep) {
-    for (int field = 0; field < 6 && rc == SSD_OK; ++field) {
+    for (int field = 0; field < 7 && rc == SSD_OK; ++field) {
       uint64_t cand[8];
       int nc = 0;
       switch (field) {
@@ -1022,7 +1109,8 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
         case 2: for (uint64_t b : {2ull, 4ull, 8ull, 16ull, 32ull}) cand[nc++] = b; break;
         case 3: for (uint64_t u : {1ull, 2ull, 4ull, 8ull}) cand[nc++] = u; break;
         case 4: if (n > 1) for (uint64_t g : {2ull, 4ull, 8ull}) cand[nc++] = g; break;
-        default: for (uint64_t c : {0ull, 1ull, 2ull}) cand[nc++] = c; break;
+        case 5: for (uint64_t c : {0ull, 1ull, 2ull}) cand[nc++] = c; break;
+        default: if (n == 1) for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
       }
       auto with = [&](uint64_t v) {
         ssd_tuning t = best;
@@ -1032,7 +1120,8 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
           case 2: t.scan_blocks_per_sm = (uint32_t)v; break;
           case 3: t.scan_unroll = (uint32_t)v; break;
           case 4: t.merge_group = (uint32_t)v; break;
-          default: t.combine_touches = (uint32_t)v; break;
+          case 5: t.combine_touches = (uint32_t)v; break;
+          default: t.collect_touches = (uint32_t)v; break;
         }
         return t;
       };

@@ -64,8 +64,9 @@ struct Tuning {
   uint32_t unroll;       // pair vectors per thread per step: 1, 2, 4, 8
   uint32_t group;        // routers loaded per lane before storing, multi-router pass: 2, 4, 8
   uint32_t combine;      // how same-word touch atomics are combined (set_touch's CM)
+  uint32_t collect;      // one-router slot: 0 = per-chunk touch lists, 1 = pre-hashed pairs re-read per chunk
 };
-inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u}; }
+inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u, 0u}; }
 
 // ---- scan (ssd_scan.cu) ----
 constexpr int kMaxBatch = SSD_MAX_ROUTERS;
@@ -220,6 +221,26 @@ cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatc
 cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, const uint2* tail, uint32_t* bits,
                                 uint64_t se0, uint64_t se_count, int grid, const Tuning& tn, cudaStream_t st);
 
+// ---- per-chunk touch lists of the fused slot (ssd_scan.cu) ----
+// Algorithm 2 for every pair of the batch, once per slot, sorted by chunk: chunk c covers the
+// estimators [c * count, (c + 1) * count) of every router, and the touch of router j, estimator
+// se, recorder x has the bit ((j * count + se - c * count) << log2_eta) | x of that chunk's bits.
+// Chunk 0's bits are set directly in `touch0`; the bit index of every touch of chunk c >= 1 is
+// appended to list c (ent + (c - 1) * cap, fill[c] entries). A pair adds at most one touch per
+// row, so a list of a chunk inside one row never holds more than the batch's pairs.
+constexpr uint32_t kMaxChunks = 32;
+struct ListArgs {
+  uint32_t log2_count;   // estimators per chunk = 2^log2_count
+  uint32_t n_chunks;     // <= kMaxChunks
+  uint64_t cap;          // entries per list
+  uint32_t* ent;         // n_chunks - 1 lists of cap entries
+  uint32_t* fill;        // kMaxChunks counters, zero before the launch
+  uint32_t* touch0;      // chunk 0's touch bits
+  DevCounters* counters; // SSD_STATUS_INTERNAL when a list would overflow (never, by the bound above)
+};
+cudaError_t launch_lists(const Dims& d, const uint32_t* tables, const ScanBatch& b, const ListArgs& a, int grid,
+                         const Tuning& tn, cudaStream_t st);
+
 // ---- one chunk of the fused slot of one router (ssd_stream.cu) ----
 // The streaming pass over estimators [se0, se0 + count) with that chunk's touch
 // bits applied; when `next` is set the same kernel collects the touch bits of the
@@ -236,6 +257,8 @@ struct ChunkArgs {
   const uint32_t* edge[2];   // head / tail pair outside the body, or nullptr
   int packed;                // vec/edge[0] hold pre-hashed pairs (edge[1] unused)
   uint32_t view;             // the router's view (raw pairs; pre-hashed pairs are already in it)
+  const uint32_t* list;      // the next chunk's touch list (bit indices), or nullptr: collect from vec
+  const uint32_t* list_fill; // its entry count (device)
 };
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st);

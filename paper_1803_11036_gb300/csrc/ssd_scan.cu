@@ -232,7 +232,111 @@ __global__ void __launch_bounds__(kBlock) k_touch_packed(const Dims d, const uin
   }
 }
 
+// Per-chunk touch lists (see ListArgs). Each block owns a contiguous range of
+// the batch's pair vectors and walks it twice: the first walk sets chunk 0's
+// bits and counts the block's touches per chunk (warp-aggregated shared-memory
+// atomics), one global atomic per chunk then reserves the block's run in each
+// list, and the second walk hashes the same pairs again and writes the bit
+// indices into the reserved runs. The range (about 40 KB at full size) is
+// still in L2 for the second walk. Every lane of a warp runs the same
+// iterations (__match_any_sync needs all 32).
+template <int CM>
+__global__ void __launch_bounds__(kBlock) k_lists(const Dims d, const uint32_t* __restrict__ tables,
+                                                  const __grid_constant__ ScanBatch b, const ListArgs a) {
+  __shared__ uint32_t sT[2048];
+  __shared__ uint32_t s_cnt[kMaxChunks], s_cur[kMaxChunks];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
+  if (threadIdx.x < kMaxChunks) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t count = 1ull << a.log2_count;
+  const uint64_t total = b.prefix[b.n];
+  uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+  per = (per + 31) & ~31ull;
+  const uint64_t v0 = (uint64_t)blockIdx.x * per;
+  const uint64_t v1 = v0 + per < total ? v0 + per : total;
+
+  // the touches of one pair (x, y) of router j: chunk 0's set (first walk), the others counted
+  // (first walk) or written (second walk)
+  auto pair = [&](uint32_t x, uint32_t y, uint32_t view, uint64_t jbase, bool live, bool write) {
+    uint32_t cip = 0, oip = 0;
+    const bool in = live && view_pair(view, x, y, cip, oip);
+    uint32_t xr = 0, c0 = 0;
+    if (in) {
+      xr = tab_hash(sT, oip) & (d.eta - 1u);
+      c0 = tab_hash(sT + 1024, cip) & d.col_mask;
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < SSD_MAX_R; ++i) {
+      if (i < d.r) {
+        uint32_t col = c0;
+        if (i) {
+          const uint32_t sh = (i - 1u) * d.delta + d.sh0;
+          col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
+        }
+        const uint64_t se = ((uint64_t)i << d.q) | col;
+        const uint32_t c = (uint32_t)(se >> a.log2_count);
+        const uint64_t bit = ((jbase + (se & (count - 1))) << d.log2_eta) | xr;
+        if (!write) set_touch<CM>(a.touch0, bit, in && c == 0);
+        const uint32_t key = (in && c != 0) ? c : 0xFFFFFFFFu;
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);
+        if (key != 0xFFFFFFFFu) {
+          const uint32_t leader = __ffs(grp) - 1u;
+          if (!write) {
+            if (lane == leader) atomicAdd(&s_cnt[key], (uint32_t)__popc(grp));
+          } else {
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&s_cur[key], (uint32_t)__popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            const uint64_t pos = (uint64_t)base + __popc(grp & lt);
+            if (pos < a.cap) a.ent[(uint64_t)(key - 1u) * a.cap + pos] = (uint32_t)bit;
+            else atomicOr(&a.counters->status, SSD_STATUS_INTERNAL);
+          }
+        }
+      }
+    }
+  };
+  auto walk = [&](bool write) {
+    for (uint64_t vb = v0 + (threadIdx.x & ~31u); vb < v1; vb += kBlock) {
+      const uint64_t v = vb + lane;
+      const bool live = v < v1;
+      uint4 w = make_uint4(0, 0, 0, 0);
+      uint64_t jb = 0;
+      uint32_t vw = 0;
+      if (live) {
+        const int j = b.n == 1 ? 0 : find_router(b, v);
+        w = write ? __ldcs(b.vec[j] + (v - b.prefix[j])) : __ldcg(b.vec[j] + (v - b.prefix[j]));
+        jb = (uint64_t)j * count;
+        vw = b.view[j];
+      }
+      pair(w.x, w.y, vw, jb, live, write);
+      pair(w.z, w.w, vw, jb, live, write);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {   // the packets outside the 16-byte bodies
+      const uint32_t* e = lane < 2u * (uint32_t)b.n ? b.edge[lane] : nullptr;
+      const uint32_t j = lane >> 1;
+      pair(e ? e[0] : 0u, e ? e[1] : 0u, e ? b.view[j] : 0u, (uint64_t)j * count, e != nullptr, write);
+    }
+  };
+  walk(false);
+  __syncthreads();
+  if (threadIdx.x >= 1 && threadIdx.x < a.n_chunks)
+    s_cur[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&a.fill[threadIdx.x], s_cnt[threadIdx.x]) : 0u;
+  __syncthreads();
+  walk(true);
+}
+
 }  // namespace
+
+cudaError_t launch_lists(const Dims& d, const uint32_t* tables, const ScanBatch& b, const ListArgs& a, int grid,
+                         const Tuning& tn, cudaStream_t st) {
+  if (a.n_chunks > kMaxChunks || b.n > 16) return cudaErrorInvalidValue;
+  if (tn.combine == 1) k_lists<1><<<grid, kBlock, 0, st>>>(d, tables, b, a);
+  else if (tn.combine == 2) k_lists<2><<<grid, kBlock, 0, st>>>(d, tables, b, a);
+  else k_lists<0><<<grid, kBlock, 0, st>>>(d, tables, b, a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prehash(const Dims& d, const uint32_t* tables, const ScanBatch& b, uint2* out, int grid,
                            cudaStream_t st) {

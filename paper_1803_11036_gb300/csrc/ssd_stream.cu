@@ -264,17 +264,27 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
   }
 }
 
+// Where a chunk launch finds the touches of the next chunk.
+constexpr int kSrcNone = 0;     // the last chunk: nothing to collect
+constexpr int kSrcRaw = 1;      // the slot's raw pairs, hashed here (tables in shared memory)
+constexpr int kSrcPacked = 2;   // the slot's pre-hashed pairs (RHFG[0] | H1 << q)
+constexpr int kSrcList = 3;     // the next chunk's touch list: bit indices written once per slot
+
 // One chunk of the fused slot of one router (eta >= 256): each warp streams
 // estimators of the chunk with their touch bits applied, counts and pools hot
-// ones and advances; with NEXT, between estimators each lane also hashes a share
-// of the slot's pairs and sets the touch bits of the next chunk (L2 atomics that
-// fill the gaps of the memory-bound stream). The pairs are walked warp by warp
-// (warp e takes vectors e*32 + lane, e*32 + lane + 32*count, ...), so every lane
-// of a warp runs the same iterations, as combine mode 1 needs.
-template <bool NEXT, bool PACKED, int CM>
+// ones and advances; unless SRC is kSrcNone, between estimators each lane also
+// sets a share of the next chunk's touch bits (L2 atomics that fill the gaps of
+// the memory-bound stream), from the next chunk's touch list or by hashing a
+// share of the slot's pairs. The pairs or list entries are walked warp by warp
+// (warp e takes e*32 + lane, e*32 + lane + 32*count, ...), so every lane of a
+// warp runs the same iterations, as combine mode 1 needs.
+template <int SRC, int CM>
 __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch s,
                                                      const __grid_constant__ ChunkArgs a) {
-  constexpr bool TABLES = NEXT && !PACKED;   // raw pairs are hashed here; pre-hashed ones are not
+  constexpr bool NEXT = SRC != kSrcNone;
+  constexpr bool PACKED = SRC == kSrcPacked;
+  constexpr bool LIST = SRC == kSrcList;
+  constexpr bool TABLES = SRC == kSrcRaw;   // raw pairs are hashed here; pre-hashed ones are not
   // Programmatic dependent launch: the next chunk's grid may be scheduled now (its blocks take
   // SM slots only as this grid's blocks exit). After the wait below, this grid reads what the
   // previous chunk wrote (this chunk's touch bits) and sets bits in the buffer the previous
@@ -301,6 +311,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
     load_group<false>(reinterpret_cast<const uint4*>(a.router), ((a.se0 + e_first) << d.log2_eta) >> 3, nullptr, 0,
                       m0, lane, v, t);
   asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous grid has completed
+  // entries of the next chunk's touch list (written by the list launch before chunk 0)
+  const uint64_t n_items = LIST ? (uint64_t)*a.list_fill : a.nvec;
   const uint32_t nr0 = NEXT ? (uint32_t)(a.nx_se0 >> d.q) : 0u;
   const uint32_t nr1 = NEXT ? (uint32_t)((a.nx_se0 + a.nx_count - 1) >> d.q) : 0u;
   const uint64_t slots = a.count * 32;   // (estimator, lane) slots sharing the pairs
@@ -322,7 +334,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   // after an estimator's pass: its share of the next chunk's touches, then its pooling
   auto finish = [&](uint64_t e, uint64_t se, uint32_t cnt, uint4 w0) {
     const uint64_t vb0 = e * 32;
-    if (NEXT) {
+    if (LIST) {
+      if (vb0 < n_items) set_touch<CM>(a.next, w0.x, vb0 + lane < n_items);
+      for (uint64_t vb = vb0 + slots; vb < n_items; vb += slots) {
+        const bool live = vb + lane < n_items;
+        set_touch<CM>(a.next, live ? __ldcs(a.list + vb + lane) : 0u, live);
+      }
+    } else if (NEXT) {
       if (vb0 < a.nvec) touch2(w0, vb0 + lane < a.nvec);
       for (uint64_t vb = vb0 + slots; vb < a.nvec; vb += slots) {
         const bool live = vb + lane < a.nvec;
@@ -343,6 +361,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   };
   // this slot's first pair vector of an estimator is loaded before its pass so the loads overlap
   auto first_pair = [&](uint64_t e) {
+    if (LIST) return make_uint4(e * 32 + lane < n_items ? __ldcs(a.list + e * 32 + lane) : 0u, 0u, 0u, 0u);
     return (NEXT && e * 32 + lane < a.nvec) ? __ldcs(a.vec + e * 32 + lane) : make_uint4(0, 0, 0, 0);
   };
   uint64_t e = e_first;
@@ -431,12 +450,12 @@ cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, 
   return cudaErrorInvalidValue;
 }
 
-template <bool NEXT, bool PACKED, int CM>
+template <int SRC, int CM>
 cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                                  cudaStream_t st) {
-  const size_t smem = (size_t)(kBlock / 32) * (d.eta >> 3) + (NEXT && !PACKED ? 2048 * 4 : 0);
+  const size_t smem = (size_t)(kBlock / 32) * (d.eta >> 3) + (SRC == kSrcRaw ? 2048 * 4 : 0);
   const uint64_t need = (a.count + (kBlock / 32) - 1) / (kBlock / 32);
-  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<NEXT, PACKED, CM>, smem, tn);
+  uint64_t grid = (uint64_t)sms * blocks_per_sm(k_chunk<SRC, CM>, smem, tn);
   if (grid > need) grid = need;
   // launched as a programmatic dependent of the previous kernel on the stream (see k_chunk)
   cudaLaunchConfig_t cfg = {};
@@ -449,20 +468,23 @@ cudaError_t launch_chunk_variant(const Dims& d, const Scratch& s, const ChunkArg
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_chunk<NEXT, PACKED, CM>, d, s, a);
+  return cudaLaunchKernelEx(&cfg, k_chunk<SRC, CM>, d, s, a);
+}
+
+template <int SRC>
+cudaError_t launch_chunk_cm(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
+                            cudaStream_t st) {
+  if (tn.combine == 1) return launch_chunk_variant<SRC, 1>(d, s, a, sms, tn, st);
+  if (tn.combine == 2) return launch_chunk_variant<SRC, 2>(d, s, a, sms, tn, st);
+  return launch_chunk_variant<SRC, 0>(d, s, a, sms, tn, st);
 }
 
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st) {
-  if (!a.next) return launch_chunk_variant<false, false, 0>(d, s, a, sms, tn, st);
-  if (a.packed) {
-    if (tn.combine == 1) return launch_chunk_variant<true, true, 1>(d, s, a, sms, tn, st);
-    if (tn.combine == 2) return launch_chunk_variant<true, true, 2>(d, s, a, sms, tn, st);
-    return launch_chunk_variant<true, true, 0>(d, s, a, sms, tn, st);
-  }
-  if (tn.combine == 1) return launch_chunk_variant<true, false, 1>(d, s, a, sms, tn, st);
-  if (tn.combine == 2) return launch_chunk_variant<true, false, 2>(d, s, a, sms, tn, st);
-  return launch_chunk_variant<true, false, 0>(d, s, a, sms, tn, st);
+  if (!a.next) return launch_chunk_variant<kSrcNone, 0>(d, s, a, sms, tn, st);
+  if (a.list) return launch_chunk_cm<kSrcList>(d, s, a, sms, tn, st);
+  if (a.packed) return launch_chunk_cm<kSrcPacked>(d, s, a, sms, tn, st);
+  return launch_chunk_cm<kSrcRaw>(d, s, a, sms, tn, st);
 }
 
 }  // namespace ssd

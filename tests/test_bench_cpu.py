@@ -29,10 +29,15 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": "Mpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
-def test_profile_traffic_needs_matching_code_and_chunk():
-    t = bench.profiled_traffic("corelink_c2", 131072)
-    assert t is not None and 1.0e9 < t < 1.3e9   # ~1.054 x the 1.074 GB a chunk launch must move
-    assert bench.profiled_traffic("corelink_c2", 262144) is None
+def test_profile_traffic_needs_matching_code_and_chunk(tmp_path):
+    prof = tmp_path / "chunk_pass_w.md"
+    prof.write_text(f"traffic_bytes_per_launch: 1.13e9\nkernel_source_sha256_16: {bench.kernel_source_hash()}\n"
+                    "chunk_estimators: 131072\n")
+    assert bench.profiled_traffic("w", 131072, str(prof)) == 1.13e9
+    assert bench.profiled_traffic("w", 262144, str(prof)) is None          # another chunk size
+    prof.write_text("traffic_bytes_per_launch: 1.13e9\nkernel_source_sha256_16: 0123456789abcdef\n"
+                    "chunk_estimators: 131072\n")
+    assert bench.profiled_traffic("w", 131072, str(prof)) is None          # the kernel changed since
     assert bench.profiled_traffic("no_such_workload", 131072) is None
 
 
