@@ -179,6 +179,24 @@ SSD_API int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group
  * hosts its columns hold, the realised column load. Reads the whole RSEA once
  * and waits for `stream`. */
 SSD_API int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream);
+/* The device address of the sketch's recorders (ssd_sketch_bytes bytes, laid
+ * out as described at the top of this file), owned by the library and valid
+ * until the sketch is destroyed. For moving a sketch between GPUs without a
+ * copy through the host (a collective library reads or writes it in place);
+ * the caller orders such access against the context's stream. */
+SSD_API int ssd_sketch_data(const ssd_sketch* s, uint16_t** d_recorders);
+/* The reduction of Algorithm 5 when the routers' RSEAs are spread over several
+ * GPUs (the paper ships every monitor server's RSEA to one server, Sec. 4):
+ * d_out[x] = min over j < n of d_in[j][x] for x < count, the elementwise
+ * minimum of the union reading (as ssd_merge). Each GPU folds the slices of
+ * one recorder range that it received from the others; collective libraries
+ * offer no 16-bit minimum, so they move the bytes and this call reduces them.
+ * d_in is a host array of n (1..SSD_MAX_ROUTERS) device pointers; d_out and
+ * every d_in[j] must be 16-byte aligned on the context's device (SSD_EINVAL
+ * otherwise; with count = 0 nothing is read). d_out may be one of the inputs.
+ * Asynchronous on `stream`. */
+SSD_API int ssd_min_merge(ssd_ctx* ctx, uint16_t* d_out, const uint16_t* const* d_in, int n, uint64_t count,
+                          void* stream);
 /* Copy `count` recorders starting at recorder `first` to dst (host or device).
  * Waits for `stream` before returning. Checkpointing a sketch is
  * export + ssd_sketch_slot; resuming is import. */

@@ -123,6 +123,21 @@ class Sketch:
               "ssd_sketch_occupancy")
         return [int(x) for x in out[: self.ctx.params.r]]
 
+    def device_view(self):
+        """The sketch's recorders as a CUDA int16 tensor sharing the library's memory (no copy;
+        the 16-bit patterns are the uint16 recorders). Valid while the sketch lives; the caller
+        orders its use against the context's stream."""
+        torch = _torch()
+        ptr = ctypes.c_void_p()
+        check(self.ctx.L.ssd_sketch_data(self._h, ctypes.byref(ptr)), "ssd_sketch_data")
+        n = self.ctx.sketch_bytes // 2
+
+        class _Recorders:
+            __cuda_array_interface__ = {"shape": (n,), "typestr": "<i2", "data": (ptr.value, False),
+                                        "version": 2, "strides": None}
+
+        return torch.as_tensor(_Recorders(), device=self.ctx.device)
+
     def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
         """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""
         n = self.ctx.sketch_bytes // 2
@@ -237,6 +252,21 @@ class Context:
         torch = _torch()
         return (torch.empty(max(cap, 1), dtype=torch.int32, device=self.device),
                 torch.empty(max(cap, 1), dtype=torch.int32, device=self.device))
+
+    def min_merge(self, out, inputs, stream=None) -> None:
+        """out[x] = min over the inputs of input[x] (ssd_min_merge): CUDA tensors of 16-bit
+        recorders on this context's device, 16-byte aligned, all as long as `out`. The reduction of
+        a merge whose routers are spread over GPUs (see shard.py)."""
+        torch = _torch()
+        for t in [out, *inputs]:
+            if not isinstance(t, torch.Tensor) or t.device != self.device or t.element_size() != 2 or \
+                    not t.is_contiguous():
+                raise ValueError("min_merge takes contiguous 16-bit CUDA tensors on the context's device")
+            if t.numel() != out.numel():
+                raise ValueError("min_merge inputs and output differ in length")
+        P = (ctypes.c_void_p * len(inputs))(*[t.data_ptr() for t in inputs])
+        check(self.L.ssd_min_merge(self._h, ctypes.c_void_p(out.data_ptr()), P, len(inputs), out.numel(),
+                                   _stream_handle(stream, self.device)), "ssd_min_merge")
 
     # -- Sec. 3.3 / 4.2 --
     def regain(self, global_sketch: Sketch, cap: int = 1 << 16, stream=None):

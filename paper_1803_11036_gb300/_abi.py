@@ -71,6 +71,8 @@ SIGNATURES = {
     "ssd_scan_batch": ([_vp, _vp, _vp, _int, _vp], _int),
     "ssd_advance": ([_vp, _int, _vp], _int),
     "ssd_merge": ([_vp, _int, _vp, _vp], _int),
+    "ssd_min_merge": ([_vp, _vp, _vp, _int, _u64, _vp], _int),
+    "ssd_sketch_data": ([_vp, ctypes.POINTER(_vp)], _int),
     "ssd_regain": ([_vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_regain_static": ([_PP, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp], _int),
     "ssd_close_slot": ([_vp, _vp, _int, _vp, _vp, _vp, _u64, _vp, _vp], _int),

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libssd.so")
-SOURCES = ["ssd_api.cu", "ssd_scan.cu", "ssd_stream.cu", "ssd_regain.cu", "ssd_static.cu", "ssd_diag.cu"]
+SOURCES = ["ssd_api.cu", "ssd_scan.cu", "ssd_stream.cu", "ssd_regain.cu", "ssd_static.cu", "ssd_diag.cu",
+           "ssd_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -455,6 +455,27 @@ int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream) {
   return SSD_OK;
 }
 
+int ssd_sketch_data(const ssd_sketch* s, uint16_t** d_recorders) {
+  if (!s || !d_recorders) return SSD_EINVAL;
+  *d_recorders = s->dr;
+  return SSD_OK;
+}
+
+int ssd_min_merge(ssd_ctx* ctx, uint16_t* d_out, const uint16_t* const* d_in, int n, uint64_t count,
+                  void* stream) {
+  if (!ctx || !d_in || n < 1 || n > SSD_MAX_ROUTERS) return SSD_EINVAL;
+  if (!count) return SSD_OK;
+  if (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u)) return SSD_EINVAL;
+  for (int j = 0; j < n; ++j)
+    if (!d_in[j] || (reinterpret_cast<uintptr_t>(d_in[j]) & 15u)) return SSD_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ssd::launch_min_ranges(d_out, d_in, n, count, ctx->sms, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "min-merge kernel");
+  ctx->launches += (count >> 3) ? 1 : 0;
+  ctx->launches += (count & 7u) ? 1 : 0;
+  return SSD_OK;
+}
+
 int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
   if (!s || (count && !dst)) return SSD_EINVAL;
   const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;

@@ -263,6 +263,11 @@ struct ChunkArgs {
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st);
 
+// ---- reduction of a merge spread over GPUs (ssd_shard.cu) ----
+// out[x] = min over j < n of in[j][x] for x < count (all 16-byte aligned; out may be an input).
+cudaError_t launch_min_ranges(uint16_t* out, const uint16_t* const* in, int n, uint64_t count, int sms,
+                              cudaStream_t st);
+
 // ---- diagnostics (ssd_diag.cu) ----
 // rk_sum[i] += sum over row i's estimators of R_k (recorders below k); eta >= 8.
 cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, unsigned long long* rk_sum, int sms,

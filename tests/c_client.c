@@ -62,6 +62,8 @@ int main(void) {
       ssd_regain_static(NULL, 0, 0, 0, NULL, NULL, NULL, NULL, 0, &u64, NULL),
       ssd_regain_static(&p, 0, 0, 0, NULL, NULL, NULL, NULL, 0, &u64, NULL),
       ssd_regain_static(&p, 2, 0, 0, NULL, NULL, NULL, NULL, 0, &u64, NULL),
+      ssd_min_merge(NULL, NULL, NULL, 1, 8, NULL),
+      ssd_sketch_data(NULL, NULL),
       ssd_close_slot(NULL, NULL, 1, NULL, NULL, NULL, 0, NULL, NULL),
       ssd_set_trace(NULL, NULL, NULL, NULL),
       ssd_slot(NULL, NULL, &pp, &u64, 1, NULL, NULL, NULL, 0, NULL, NULL),
