@@ -419,6 +419,14 @@ SSD_API const char* ssd_strerror(int code);
 SSD_API const char* ssd_last_cuda_error(void);
 /* ABI version, major * 100 + minor. */
 SSD_API int ssd_version(void);
+/* How the library was built: SSD_BUILD_DEBUG when it is the debug build, whose
+ * kernels check their indices against their bounds (a recorder inside its
+ * estimator, a column inside its row, a touch bit inside its buffer, a pool,
+ * bucket or candidate index inside its capacity), skip an access that breaks
+ * one and report it as SSD_STATUS_INTERNAL in ssd_stats_get, which also checks
+ * guard words around the candidate tuple buffers. The release build returns 0. */
+#define SSD_BUILD_DEBUG 1
+SSD_API int ssd_build_flags(void);
 
 #ifdef __cplusplus
 }

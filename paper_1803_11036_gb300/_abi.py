@@ -89,14 +89,20 @@ SIGNATURES = {
     "ssd_strerror": ([_int], ctypes.c_char_p),
     "ssd_last_cuda_error": ([], ctypes.c_char_p),
     "ssd_version": ([], _int),
+    "ssd_build_flags": ([], _int),
 }
 
 _lock = threading.Lock()
 _lib = None
 
 
+def debug_requested() -> bool:
+    """SSD_DEBUG=1 in the environment selects the debug build of the library."""
+    return os.environ.get("SSD_DEBUG", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_requested() else _build.LIB
 
 
 def load():
@@ -104,10 +110,11 @@ def load():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if _build.stale():
+            dbg = debug_requested()
+            path = lib_path()
+            if _build.stale(dbg):
                 try:
-                    path = _build.build()
+                    path = _build.build(debug=dbg)
                 except Exception as e:  # no toolchain: nothing to fall back to
                     raise ImportError(f"the CUDA library {path} is missing and could not be built: {e}") from e
             if not os.path.exists(path):

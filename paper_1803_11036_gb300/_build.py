@@ -3,6 +3,11 @@
 Each translation unit compiles in parallel, then nvcc links the shared
 object into ``paper_1803_11036_gb300/_build/``. No cmake, no torch extension
 machinery: the library is plain C ABI over CUDA.
+
+``build(debug=True)`` makes the debug library in ``_build/debug/`` (compiled
+with -DSSD_DEBUG=1: device bound checks that report instead of faulting, guard
+words around the candidate buffers); the binding loads it when the
+environment sets SSD_DEBUG=1.
 """
 from __future__ import annotations
 
@@ -17,6 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libssd.so")
+BUILD_DEBUG = os.path.join(BUILD, "debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libssd.so")
 SOURCES = ["ssd_api.cu", "ssd_scan.cu", "ssd_stream.cu", "ssd_regain.cu", "ssd_static.cu", "ssd_diag.cu",
            "ssd_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,22 +47,26 @@ def _deps():
     return deps
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Build libssd.so if a source is newer than it; returns its path."""
-    if not force and not stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Build libssd.so (or the debug library) if a source is newer than it; returns its path."""
+    out_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and not stale(debug):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug:
+        extra += ["-DSSD_DEBUG=1"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [nvcc(), *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, obj, r
@@ -67,16 +78,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode:
             raise RuntimeError(f"nvcc failed on {src}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[o for _, o, _ in results],
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("nvcc link failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

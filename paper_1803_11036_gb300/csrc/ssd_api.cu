@@ -52,6 +52,10 @@ struct ssd_ctx {
   uint64_t hs_calls;
   cudaEvent_t ev_hs_free[2], ev_hs_copied;
   uint64_t epoch;   // ssd_buffer_epoch: bumped when a buffer captured work may hold is replaced
+  // debug build only: the status word of the kernels' bound checks and the candidate tuple
+  // buffers' allocations with their guard words (ctb[i] = ctb_alloc[i] + kGuardWords)
+  unsigned int* dbg;
+  uint32_t* ctb_alloc[2];
 };
 
 struct ssd_sketch {
@@ -65,6 +69,10 @@ struct ssd_sketch {
 namespace {
 
 thread_local char g_cuda_err[256] = "";
+
+// Guard words before and after each candidate tuple buffer in the debug build.
+constexpr uint64_t kGuardWords = SSD_DEBUG ? 64 : 0;
+constexpr uint32_t kGuard = 0xC0DEC0DEu;
 
 int cuda_fail(cudaError_t e, const char* where) {
   std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
@@ -223,8 +231,8 @@ void free_ctx(ssd_ctx* c) {
   cudaFree(c->pool_col);
   cudaFree(c->pool_rk);
   cudaFree(c->pool_bm);
-  cudaFree(c->ctb[0]);
-  cudaFree(c->ctb[1]);
+  for (int i = 0; i < 2; ++i) cudaFree(c->ctb_alloc[i]);
+  cudaFree(c->dbg);
   cudaFree(c->stage);
   cudaFree(c->counters);
   cudaFree(c->bucket_off);
@@ -318,8 +326,9 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
       {(void**)&c->pool_col, R * d.hse_cap * 4},
       {(void**)&c->pool_rk, R * d.hse_cap * 4},
       {(void**)&c->pool_bm, R * d.hse_cap * (uint64_t)d.words * 4},
-      {(void**)&c->ctb[0], d.ctb_cap * R * 4},
-      {(void**)&c->ctb[1], d.ctb_cap * R * 4},
+      {(void**)&c->ctb_alloc[0], (d.ctb_cap * R + 2 * kGuardWords) * 4},
+      {(void**)&c->ctb_alloc[1], (d.ctb_cap * R + 2 * kGuardWords) * 4},
+      {(void**)&c->dbg, SSD_DEBUG ? 4 : 0},
       {(void**)&c->stage, d.out_cap * 8},
       {(void**)&c->counters, sizeof(ssd::DevCounters)},
       {(void**)&c->n_out, 8},
@@ -336,7 +345,20 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
       return SSD_ENOMEM;
     }
   }
+  for (int i = 0; i < 2; ++i) c->ctb[i] = c->ctb_alloc[i] + kGuardWords;
+  d.touch_bits = c->touch_bytes * 8;
+  d.dbg = c->dbg;
   e = cudaMemcpy(c->tables, tables, 2048 * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && SSD_DEBUG) {
+    e = cudaMemset(c->dbg, 0, 4);
+    uint32_t guard[kGuardWords ? kGuardWords : 1];
+    for (auto& g : guard) g = kGuard;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaMemcpy(c->ctb_alloc[i], guard, kGuardWords * 4, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(c->ctb[i] + d.ctb_cap * R, guard, kGuardWords * 4, cudaMemcpyHostToDevice);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(ssd::DevCounters));
   // touch bits start (and are left by every fused slot) all zero
   if (e == cudaSuccess) e = cudaMemset(c->touch[0], 0, c->touch_bytes);
@@ -1010,8 +1032,24 @@ int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
   out->level[0] = out->hot[0];
   out->raw = h.raw;
   out->n_out = h.n_out;
+  if (SSD_DEBUG) {   // the kernels' bound checks and the candidate buffers' guard words
+    unsigned int dbg = 0;
+    SSD_CUDA(cudaMemcpy(&dbg, ctx->dbg, 4, cudaMemcpyDeviceToHost));
+    out->status |= dbg;
+    uint32_t g[kGuardWords ? kGuardWords : 1];
+    const uint64_t words = ctx->d.ctb_cap * ctx->d.r;
+    for (int i = 0; i < 2; ++i) {
+      for (const uint32_t* at : {ctx->ctb_alloc[i], ctx->ctb[i] + words}) {
+        SSD_CUDA(cudaMemcpy(g, at, kGuardWords * 4, cudaMemcpyDeviceToHost));
+        for (uint64_t w = 0; w < kGuardWords; ++w)
+          if (g[w] != kGuard) out->status |= SSD_STATUS_INTERNAL;
+      }
+    }
+  }
   return SSD_OK;
 }
+
+int ssd_build_flags(void) { return SSD_DEBUG ? SSD_BUILD_DEBUG : 0; }
 
 uint64_t ssd_launch_count(const ssd_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -1063,6 +1101,7 @@ int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
       ctx->touch[i] = nb[i];
     }
     ctx->touch_bytes = bytes;
+    ctx->d.touch_bits = bytes * 8;
     ctx->epoch += 1;
   }
   ctx->tn.stream_bps = t->stream_blocks_per_sm;

@@ -6,6 +6,15 @@
 
 #include "ssd.h"
 
+// The debug build (nvcc -DSSD_DEBUG=1, a separate library): the kernel indices with a stated
+// bound (a recorder inside its estimator, a column inside its row, a touch bit inside its buffer,
+// a pool, bucket or candidate index inside its capacity) are checked before the access;
+// a broken bound skips the access and records SSD_STATUS_INTERNAL instead of faulting, and guard
+// words around the candidate tuple buffers are compared when the counters are read.
+#ifndef SSD_DEBUG
+#define SSD_DEBUG 0
+#endif
+
 namespace ssd {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;  // "not hot" in the per-estimator pool index
@@ -33,7 +42,24 @@ struct Dims {
   uint32_t hse_cap;    // pool entries per row
   uint64_t ctb_cap;    // tuples per candidate buffer
   uint64_t out_cap;    // staged accepted tuples (a power of two)
+  uint64_t touch_bits; // bits of one touch buffer (debug bound)
+  unsigned int* dbg;   // debug build: device word collecting SSD_STATUS_INTERNAL (nullptr otherwise)
 };
+
+// True when `ok`; in the debug build a false `ok` also records SSD_STATUS_INTERNAL, and the caller
+// skips the access it guards. The release build compiles the check away (always true).
+__device__ __forceinline__ bool in_bounds(const Dims& d, bool ok) {
+#if SSD_DEBUG
+  if (!ok) {
+    if (d.dbg) atomicOr(d.dbg, SSD_STATUS_INTERNAL);
+    return false;
+  }
+#else
+  (void)d;
+  (void)ok;
+#endif
+  return true;
+}
 
 // Scratch of a context (all device memory).
 struct Scratch {
@@ -188,7 +214,8 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
     const bool ok = live && e < count;
     if (ok && x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
-    set_touch<CM>(bits, ((jbase + e) << d.log2_eta) | x, ok);
+    const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
+    set_touch<CM>(bits, bit, ok && in_bounds(d, bit < d.touch_bits));
   }
 }
 
@@ -205,7 +232,9 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    set_touch<CM>(bits, (e << d.log2_eta) | x, live && e < count);
+    const uint64_t bit = (e << d.log2_eta) | x;
+    const bool ok = live && e < count;
+    set_touch<CM>(bits, bit, ok && in_bounds(d, bit < d.touch_bits && x < d.eta));
   }
 }
 

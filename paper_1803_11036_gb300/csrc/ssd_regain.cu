@@ -424,7 +424,10 @@ __device__ __forceinline__ void level_hit(const Dims& d, const Scratch& s, uint3
 __device__ __forceinline__ uint32_t load_candidate(const Dims& d, const Scratch& s, uint32_t i, const uint32_t* tup,
                                                    uint32_t (&tl)[SSD_MAX_R]) {
 #pragma unroll
-  for (uint32_t j = 0; j < SSD_MAX_R; ++j) tl[j] = j < i ? tup[j] : 0u;
+  for (uint32_t j = 0; j < SSD_MAX_R; ++j) {
+    tl[j] = j < i ? tup[j] : 0u;
+    if (!in_bounds(d, tl[j] < d.hse_cap)) tl[j] = 0;   // a pool index past the pool
+  }
   const uint32_t he0 = s.pool_col[tl[0]];
   uint32_t tp = 0;
 #pragma unroll
@@ -458,6 +461,7 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
         const uint32_t low = load_candidate(d, s, i, rctb + c * d.r, tl);
         b = off[low];
         e = off[low + 1];
+        if (!in_bounds(d, b <= e && e <= d.hse_cap)) b = e = 0;
       }
       for (uint32_t p = 0; __any_sync(kFull, b + p < e); ++p)
         level_hit(d, s, i, sctb, tl, b + p < e ? ent[b + p] : kNone, lane, view);
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(kBlock) k_level(const Dims d, const Scratch s,
     if (item < total) {
       const uint32_t h = (uint32_t)(item & ((1u << d.delta) - 1u));
       const uint32_t he_i = (h << d.low_bits) | load_candidate(d, s, i, rctb + (item >> d.delta) * d.r, tl);
-      idx = s.hot_idx[((uint64_t)i << d.q) | he_i];
+      idx = in_bounds(d, he_i < (1u << d.q)) ? s.hot_idx[((uint64_t)i << d.q) | he_i] : kNone;
     }
     level_hit(d, s, i, sctb, tl, idx, lane, view);
   }

@@ -16,14 +16,14 @@ __device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t ci
                                           const uint32_t* sT, const Dims& d) {
   const uint32_t j = tab_hash(sT, oip) & (d.eta - 1u);
   const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
-  dr[((uint64_t)c0 << d.log2_eta) | j] = 0;
+  if (in_bounds(d, j < d.eta && c0 < (1u << d.q))) dr[((uint64_t)c0 << d.log2_eta) | j] = 0;
 #pragma unroll
   for (uint32_t i = 1; i < SSD_MAX_R; ++i) {
     if (i < d.r) {
       const uint32_t sh = (i - 1u) * d.delta + d.sh0;
       const uint32_t w = sh < 32u ? (cip >> sh) : 0u;
       const uint32_t col = (w ^ c0) & d.col_mask;
-      dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = 0;
+      if (in_bounds(d, col < (1u << d.q))) dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = 0;
     }
   }
 }
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_lists(const Dims d, const uint32_t* 
         const uint64_t se = ((uint64_t)i << d.q) | col;
         const uint32_t c = (uint32_t)(se >> a.log2_count);
         const uint64_t bit = ((jbase + (se & (count - 1))) << d.log2_eta) | xr;
-        if (!write) set_touch<CM>(a.touch0, bit, in && c == 0);
+        if (!write) set_touch<CM>(a.touch0, bit, in && c == 0 && in_bounds(d, bit < d.touch_bits));
         const uint32_t key = (in && c != 0) ? c : 0xFFFFFFFFu;
         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);
         if (key != 0xFFFFFFFFu) {

@@ -80,7 +80,7 @@ extern "C" int ssd_regain_static(const ssd_params* p, uint32_t side, uint32_t gr
   if (ssd_params_check(p) != SSD_OK) return SSD_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return SSD_ECUDA;
-  ssd::Dims d;
+  ssd::Dims d{};
   d.log2_eta = p->log2_eta; d.q = p->q; d.r = p->r; d.delta = p->delta; d.k = p->k; d.flags = p->flags;
   if (ssd_threshold(p, &d.thr) != SSD_OK) return SSD_EINVAL;
   d.eta = 1u << p->log2_eta;
@@ -108,6 +108,8 @@ extern "C" int ssd_regain_static(const ssd_params* p, uint32_t side, uint32_t gr
   s.counters = reinterpret_cast<ssd::DevCounters*>(b + pl.counters);
   s.bucket_off = s.bucket_cnt = s.bucket_ent = nullptr;   // no room for the bucket index: probe hot_idx
   unsigned long long* nd = reinterpret_cast<unsigned long long*>(b + pl.n_out);
+  d.touch_bits = 0;                          // no touch bits on this path
+  d.dbg = SSD_DEBUG ? &s.counters->status : nullptr;
 
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSD_ECUDA;

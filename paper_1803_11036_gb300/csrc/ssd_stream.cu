@@ -142,7 +142,7 @@ __device__ __forceinline__ void pool_if_hot(const Dims& d, const Scratch& s, uin
       }
     }
   }
-  if (lane == 0) s.hot_idx[se] = idx;
+  if (lane == 0 && in_bounds(d, se < ((uint64_t)d.r << d.q))) s.hot_idx[se] = idx;
   __syncwarp();
 }
 
@@ -335,10 +335,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   auto finish = [&](uint64_t e, uint64_t se, uint32_t cnt, uint4 w0) {
     const uint64_t vb0 = e * 32;
     if (LIST) {
-      if (vb0 < n_items) set_touch<CM>(a.next, w0.x, vb0 + lane < n_items);
+      if (vb0 < n_items)
+        set_touch<CM>(a.next, w0.x, vb0 + lane < n_items && in_bounds(d, w0.x < d.touch_bits));
       for (uint64_t vb = vb0 + slots; vb < n_items; vb += slots) {
         const bool live = vb + lane < n_items;
-        set_touch<CM>(a.next, live ? __ldcs(a.list + vb + lane) : 0u, live);
+        const uint32_t bit = live ? __ldcs(a.list + vb + lane) : 0u;
+        set_touch<CM>(a.next, bit, live && in_bounds(d, bit < d.touch_bits));
       }
     } else if (NEXT) {
       if (vb0 < a.nvec) touch2(w0, vb0 + lane < a.nvec);

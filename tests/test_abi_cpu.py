@@ -89,3 +89,16 @@ def test_create_without_gpu_fails_cleanly():
     rc = L.ssd_create(ctypes.byref(p), tables.ctypes.data, 0, ctypes.byref(h))
     assert rc in (_abi.SSD_ECUDA, _abi.SSD_EINVAL)
     assert not h.value
+
+
+def test_debug_build_compiles_and_says_so():
+    """The debug library (-DSSD_DEBUG=1) builds for sm_103a, exports the same ABI and reports
+    itself; the release library does not."""
+    from paper_1803_11036_gb300 import _build
+    path = _build.build(debug=True)
+    D = ctypes.CDLL(path)
+    D.ssd_build_flags.restype = ctypes.c_int
+    assert D.ssd_build_flags() == 1
+    for n in declared_symbols():
+        assert hasattr(D, n), n
+    assert _abi.load().ssd_build_flags() == 0
