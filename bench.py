@@ -527,12 +527,17 @@ def paper_c1_leg(rank: int, local: int, warmup: int = 3, steps: int = 30) -> dic
 
 
 def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64, per_router: int = 4,
-               offered_per_s: float = 500.0, max_inflight: int = 16, tuning: dict | None = None) -> dict:
+               rates=(500.0, 2000.0, None), max_inflight: int = 16, tuning: dict | None = None) -> dict:
     """Routers stream slices at Poisson times; each slice is scanned and closed on its router's
     resident RSEA as soon as the device has room (continuous batching, at most max_inflight in
     flight). Latency runs from a slice's arrival to its list on the host. Slices arrive in
     pinned buffers that have crossed the host link once before the clock starts, as the
-    reused receive buffers of a deployment would have."""
+    reused receive buffers of a deployment would have.
+
+    The same slices run at each offered rate of `rates` (None: every slice ready at once, the
+    saturated capacity), each time on freshly admitted routers, and then through the plain form:
+    one slice at a time, each call waited for before the next (max_inflight 1), at the first rate
+    and saturated. The plain lists must equal the served ones, router by router, slot by slot."""
     import torch
 
     import paper_1803_11036_gb300 as ssd
@@ -542,8 +547,7 @@ def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64
     W = replica_workload(name, rank)
     dev = torch.device("cuda", local)
     rng = np.random.default_rng(11 + rank)
-    gap = routers / offered_per_s          # mean gap between one router's slices
-    slices = []
+    base = []   # (router, seq, pinned pairs, unit-rate arrival)
     for r in range(routers):
         tr = dict(W["traffic"])
         tr["seed"] = tr["seed"] + 101 * r
@@ -551,28 +555,53 @@ def served_leg(rank: int, local: int, name: str = "served_c5", routers: int = 64
         views = T.fill_many([(j, 0) for j in range(per_router)])
         t = 0.0
         for j, v in enumerate(views):
-            t += rng.exponential(gap)
-            host = torch.from_numpy(v.reshape(-1).view(np.int32)).pin_memory()
-            slices.append(serve.Slice(router=r, pairs=host, arrival=t, seq=j))
-    warm = torch.empty(max(s.pairs.numel() for s in slices), dtype=torch.int32, device=dev)
-    for s in slices:
-        warm[:s.pairs.numel()].copy_(s.pairs, non_blocking=True)
+            t += rng.exponential(routers)     # one slice per second overall at rate 1
+            base.append((r, j, torch.from_numpy(v.reshape(-1).view(np.int32)).pin_memory(), t))
+    warm = torch.empty(max(b[2].numel() for b in base), dtype=torch.int32, device=dev)
+    for b in base:
+        warm[:b[2].numel()].copy_(b[2], non_blocking=True)
     torch.cuda.synchronize(dev)
     del warm
-    srv = serve.Server(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]), device=local,
-                       max_inflight=max_inflight, max_slice_pairs=int(W["traffic"]["count_b"]), tuning=tuning)
-    for r in range(routers):               # admit every router before the clock starts
-        if not srv.try_admit(r):
-            break
-    admitted = len(srv.tenants)
-    res = srv.run([s for s in slices if s.router in srv.tenants])
-    srv.close()
-    out = serve.latency_summary(res)
-    out.update({"workload": name, "routers": admitted, "q": W["params"]["q"],
-                "offered_slices_per_s": offered_per_s, "max_inflight": max_inflight,
-                "slice_packets": "uniform [10k, 2M]", "reserved_slice_pairs": int(W["traffic"]["count_b"]),
-                "tuning": tuning or "default"})
-    return out
+
+    def run(rate, inflight):
+        slices = [serve.Slice(router=r, pairs=pr, arrival=(t / rate if rate else 0.0), seq=j) for r, j, pr, t in base]
+        srv = serve.Server(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]), device=local,
+                           max_inflight=inflight, max_slice_pairs=int(W["traffic"]["count_b"]), tuning=tuning)
+        for r in range(routers):               # admit every router before the clock starts
+            if not srv.try_admit(r):
+                break
+        admitted = len(srv.tenants)
+        res = srv.run([s for s in slices if s.router in srv.tenants], realtime=rate is not None)
+        srv.close()
+        torch.cuda.empty_cache()
+        out = serve.latency_summary(res)
+        out.update({"offered_slices_per_s": rate if rate else "all at once", "max_inflight": inflight,
+                    "routers": admitted})
+        return out, {(x.router, x.slot): (x.ips, x.rk) for x in res}
+
+    served, lists = [], None
+    for rate in rates:
+        o, l = run(rate, max_inflight)
+        served.append(o)
+        lists = lists or l
+    plain = []
+    same = True
+    for rate in (rates[0], None):
+        o, l = run(rate, 1)
+        plain.append(o)
+        same = same and set(l) == set(lists) and all(
+            np.array_equal(l[k][0], lists[k][0]) and np.array_equal(l[k][1], lists[k][1]) for k in lists)
+    sat_served = next(x for x in served if x["offered_slices_per_s"] == "all at once")
+    sat_plain = plain[-1]
+    first = dict(served[0])
+    first.update({"workload": name, "q": W["params"]["q"], "slice_packets": "uniform [10k, 2M]",
+                  "reserved_slice_pairs": int(W["traffic"]["count_b"]), "tuning": tuning or "default",
+                  "by_offered_rate": served, "plain": plain, "identical_lists_plain_vs_served": bool(same),
+                  "capacity_mpps": {"served": sat_served["mpps"], "plain": sat_plain["mpps"],
+                                    "speedup": round(sat_served["mpps"] / sat_plain["mpps"], 3)},
+                  "note": "plain = the same slices one at a time (each ssd_slot_host call waited for before "
+                          "the next); capacity = every slice ready at once"})
+    return first
 
 
 def run_ours(args, world, rank, local):
