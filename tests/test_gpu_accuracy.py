@@ -63,3 +63,52 @@ def test_fpr_fnr_against_exact_counts(wl):
     assert out["eq2_as_printed"]["TFR"] < 0.5
     for c in ctxs.values():
         c.close()
+
+
+def test_sliding_accuracy_over_three_windows():
+    """Sec. 5's sliding-window experiment on synthetic core-link traffic at 1/16 scale (390,625
+    packets per slot, 62,500 sources, 50 planted hosts of 1,500-50,000 peers switching on and off
+    mid-window; q = 14 keeps the column load of the full size): k = 60 slots run for 3k = 180 slots,
+    the rates taken against the exact counts at every 5th window end once the window is full
+    (25 windows). Three readings side by side: the literal list, the RHFG[0]-checked list and
+    Eq. 2 as printed."""
+    W = tg.workload("corelink_acc")
+    prm = W["params"]
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    k = prm["k"]
+    modes = (("literal", 0), ("verify", ssd.SSD_VERIFY_H0), ("eq2_as_printed", ssd.SSD_RHFG_LITERAL))
+    ctxs = {m: ssd.Context(ssd.make_params(prm, f), tabs) for m, f in modes}
+    sk = {m: c.sketch() for m, c in ctxs.items()}
+    ex = oracle.Exact(k, prm["theta"])
+    per = {m: [] for m in ctxs}
+    rows = []
+    for t in range(W["slots"]):
+        pairs = T.slot(t)[0]
+        ex.add_slot(pairs)
+        dev = to_dev(pairs)
+        got = {m: c.slot([sk[m]], [dev])[0] for m, c in ctxs.items()}
+        if t >= k - 1 and (t - (k - 1)) % 5 == 0:
+            truth, _ = ex.report()
+            assert set(got["verify"].tolist()) <= set(got["literal"].tolist())
+            row = [t - k + 1, len(truth)]
+            for m in ctxs:
+                r = rates(got[m], truth)
+                per[m].append(r)
+                row += [round(r[0], 4), round(r[1], 4)]
+            rows.append(row)
+    out = {}
+    for m, v in per.items():
+        a = np.array(v)
+        out[m] = dict(FPR=round(float(a[:, 0].mean()), 4), FNR=round(float(a[:, 1].mean()), 4),
+                      TFR=round(float(a.sum(axis=1).mean()), 4), FPR_max=round(float(a[:, 0].max()), 4),
+                      FNR_max=round(float(a[:, 1].max()), 4), windows=len(v))
+    print("\nwindow SW(i,60) | true SPs | literal FPR FNR | checked FPR FNR | Eq.2 as printed FPR FNR")
+    for row in rows:
+        print(" ".join(str(x) for x in row))
+    print(f"corelink_acc sliding accuracy: {out}")
+    assert len(rows) == 25 and min(r[1] for r in rows) > 10
+    assert out["verify"]["FPR"] <= out["literal"]["FPR"]
+    assert out["verify"]["TFR"] < 0.2 and out["eq2_as_printed"]["TFR"] < 0.2
+    for c in ctxs.values():
+        c.close()

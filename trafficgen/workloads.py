@@ -62,6 +62,14 @@ WORKLOADS = {
         traffic=dict(seed=1012, n_src=250_000, zipf_s=1.1, deg_cap=512, rho=0.3, n_planted=50,
                      planted_lo=1500, planted_hi=50_000, k=60, planted_mode=1, count="fixed",
                      count_a=1_562_500)),
+    # The core-link recipe at 1/16 scale (packets, sources, planted hosts; q=14 keeps the column
+    # load near the full size's) for three windows of 60 slots: the long sliding-window accuracy
+    # run against the exact counts (the precise algorithm is too slow for full-size windows).
+    "corelink_acc": dict(
+        params=_p(11, 14, 5, 6, 60, 1024), hash_seed=32, slots=180,
+        traffic=dict(seed=3002, n_src=62_500, zipf_s=1.1, deg_cap=512, rho=0.3, n_planted=50,
+                     planted_lo=1500, planted_hi=50_000, k=60, planted_mode=1, count="fixed",
+                     count_a=390_625)),
     # ---- reduced sizes of the same recipes (element-by-element parity) ----
     "corelink_small": dict(
         params=_p(11, 14, 5, 6, 8, 1024), hash_seed=22, slots=14,
