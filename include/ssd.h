@@ -345,7 +345,7 @@ SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
  * these choices set only how the work of Algorithms 2 and 5 and of the
  * streaming pass (Sec. 4.3) is spread over the GPU. No value changes a
  * recorder, a list or a counter. Defaults: touch_chunk_bytes of the params, 0, 8,
- * 4, 8, 0, 0.
+ * 4, 8, 0, 0, 0.
  *   touch_chunk_bytes: touch bits of one chunk of ssd_slot (64 KiB .. 1 GiB,
  *       rounded up to 256 B; chunk sizes are powers of two that fit it);
  *   stream_blocks_per_sm: resident blocks per SM of the streaming and chunk
@@ -367,7 +367,13 @@ SSD_API int ssd_reserve(ssd_ctx* ctx, uint64_t max_pairs);
  *       pair once per slot, sets chunk 0's touch bits and writes the bit index
  *       of every other touch into its chunk's list (4 bytes per touch), so each
  *       chunk launch reads only its own touches; 1 = the slot's pairs, hashed
- *       once into (RHFG[0], H1) words, are re-read by every chunk launch. */
+ *       once into (RHFG[0], H1) words, are re-read by every chunk launch;
+ *   pair_level: how the pair level of the regain (HSE(0) x HSE(1), Sec. 4.2)
+ *       computes the R_k of each pair's union. 0 = on the tensor cores, where it
+ *       applies (eta a multiple of 128, pruning on): the popcounts of the ANDed
+ *       "recorder < k" bitmaps are one matrix product of the bitmaps read as
+ *       0/1 vectors, computed exactly as an fp8 GEMM with f32 sums; 1 = AND and
+ *       popcount on the CUDA cores. */
 typedef struct ssd_tuning {
   uint64_t touch_chunk_bytes;
   uint32_t stream_blocks_per_sm;
@@ -376,6 +382,8 @@ typedef struct ssd_tuning {
   uint32_t merge_group;
   uint32_t combine_touches;
   uint32_t collect_touches;
+  uint32_t pair_level;
+  uint32_t reserved; /* must be 0 */
 } ssd_tuning;
 
 /* The context's current launch configuration (host only). */

@@ -41,11 +41,12 @@ class Tuning(ctypes.Structure):
     _fields_ = [("touch_chunk_bytes", ctypes.c_uint64), ("stream_blocks_per_sm", ctypes.c_uint32),
                 ("scan_blocks_per_sm", ctypes.c_uint32), ("scan_unroll", ctypes.c_uint32),
                 ("merge_group", ctypes.c_uint32), ("combine_touches", ctypes.c_uint32),
-                ("collect_touches", ctypes.c_uint32)]
+                ("collect_touches", ctypes.c_uint32), ("pair_level", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 TUNING_FIELDS = ("touch_chunk_bytes", "stream_blocks_per_sm", "scan_blocks_per_sm", "scan_unroll", "merge_group",
-                 "combine_touches", "collect_touches")
+                 "combine_touches", "collect_touches", "pair_level")
 
 
 # name -> (argtypes, restype); the exported ABI, in header order

@@ -193,7 +193,8 @@ int trace(ssd_ctx* ctx, cudaEvent_t ev, cudaStream_t st) {
 int regain_after_pass(ssd_ctx* ctx, uint32_t* ips, uint32_t* rk, uint64_t cap, unsigned long long* n_out,
                       cudaStream_t st, uint32_t view) {
   int launches = 0;
-  cudaError_t e = ssd::launch_regain_tail(ctx->d, ctx->s, ips, rk, cap, n_out, ctx->sms, st, &launches, view);
+  cudaError_t e = ssd::launch_regain_tail(ctx->d, ctx->s, ips, rk, cap, n_out, ctx->sms, st, &launches, view,
+                                          ctx->tn.pair_level == 0);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(e, "regain kernels");
   return SSD_OK;
@@ -349,9 +350,10 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
   d.touch_bits = c->touch_bytes * 8;
   d.dbg = c->dbg;
   e = cudaMemcpy(c->tables, tables, 2048 * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && SSD_DEBUG) {
+#if SSD_DEBUG
+  if (e == cudaSuccess) {
     e = cudaMemset(c->dbg, 0, 4);
-    uint32_t guard[kGuardWords ? kGuardWords : 1];
+    uint32_t guard[kGuardWords];
     for (auto& g : guard) g = kGuard;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
       e = cudaMemcpy(c->ctb_alloc[i], guard, kGuardWords * 4, cudaMemcpyHostToDevice);
@@ -359,6 +361,7 @@ int ssd_create(const ssd_params* p, const uint32_t* tables, int device, ssd_ctx*
         e = cudaMemcpy(c->ctb[i] + d.ctb_cap * R, guard, kGuardWords * 4, cudaMemcpyHostToDevice);
     }
   }
+#endif
   if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(ssd::DevCounters));
   // touch bits start (and are left by every fused slot) all zero
   if (e == cudaSuccess) e = cudaMemset(c->touch[0], 0, c->touch_bytes);
@@ -1032,7 +1035,8 @@ int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
   out->level[0] = out->hot[0];
   out->raw = h.raw;
   out->n_out = h.n_out;
-  if (SSD_DEBUG) {   // the kernels' bound checks and the candidate buffers' guard words
+#if SSD_DEBUG
+  {   // the kernels' bound checks and the candidate buffers' guard words
     unsigned int dbg = 0;
     SSD_CUDA(cudaMemcpy(&dbg, ctx->dbg, 4, cudaMemcpyDeviceToHost));
     out->status |= dbg;
@@ -1046,6 +1050,7 @@ int ssd_stats_get(ssd_ctx* ctx, ssd_stats* out, void* stream) {
       }
     }
   }
+#endif
   return SSD_OK;
 }
 
@@ -1065,11 +1070,12 @@ int ssd_tuning_get(const ssd_ctx* ctx, ssd_tuning* out) {
   out->merge_group = ctx->tn.group;
   out->combine_touches = ctx->tn.combine;
   out->collect_touches = ctx->tn.collect;
+  out->pair_level = ctx->tn.pair_level;
   return SSD_OK;
 }
 
 int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
-  if (!ctx || !t || t->collect_touches > 1) return SSD_EINVAL;
+  if (!ctx || !t || t->collect_touches > 1 || t->pair_level > 1 || t->reserved) return SSD_EINVAL;
   if (t->touch_chunk_bytes < (64ull << 10) || t->touch_chunk_bytes > (1ull << 30)) return SSD_EINVAL;
   if (t->stream_blocks_per_sm > 8 || t->scan_blocks_per_sm < 1 || t->scan_blocks_per_sm > 32) return SSD_EINVAL;
   const uint32_t u = t->scan_unroll, g = t->merge_group;
@@ -1110,6 +1116,7 @@ int ssd_tuning_set(ssd_ctx* ctx, const ssd_tuning* t) {
   ctx->tn.group = g;
   ctx->tn.combine = t->combine_touches;
   ctx->tn.collect = t->collect_touches;
+  ctx->tn.pair_level = t->pair_level;
   return SSD_OK;
 }
 
@@ -1160,7 +1167,7 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
   ssd_tuning best = start;
   int rc = SSD_OK;
   for (int sweep = 0; sweep < 2 && rc == SSD_OK; ++sweep) {
-    for (int field = 0; field < 7 && rc == SSD_OK; ++field) {
+    for (int field = 0; field < 8 && rc == SSD_OK; ++field) {
       uint64_t cand[8];
       int nc = 0;
       switch (field) {
@@ -1170,7 +1177,8 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
         case 3: for (uint64_t u : {1ull, 2ull, 4ull, 8ull}) cand[nc++] = u; break;
         case 4: if (n > 1) for (uint64_t g : {2ull, 4ull, 8ull}) cand[nc++] = g; break;
         case 5: for (uint64_t c : {0ull, 1ull, 2ull}) cand[nc++] = c; break;
-        default: if (n == 1) for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
+        case 6: if (n == 1) for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
+        default: for (uint64_t c : {0ull, 1ull}) cand[nc++] = c; break;
       }
       auto with = [&](uint64_t v) {
         ssd_tuning t = best;
@@ -1181,7 +1189,8 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
           case 3: t.scan_unroll = (uint32_t)v; break;
           case 4: t.merge_group = (uint32_t)v; break;
           case 5: t.combine_touches = (uint32_t)v; break;
-          default: t.collect_touches = (uint32_t)v; break;
+          case 6: t.collect_touches = (uint32_t)v; break;
+          default: t.pair_level = (uint32_t)v; break;
         }
         return t;
       };

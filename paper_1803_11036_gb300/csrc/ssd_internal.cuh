@@ -91,8 +91,9 @@ struct Tuning {
   uint32_t group;        // routers loaded per lane before storing, multi-router pass: 2, 4, 8
   uint32_t combine;      // how same-word touch atomics are combined (set_touch's CM)
   uint32_t collect;      // one-router slot: 0 = per-chunk touch lists, 1 = pre-hashed pairs re-read per chunk
+  uint32_t pair_level;   // 0 = the pair level on the tensor cores where it applies, 1 = CUDA-core tiles
 };
-inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u, 0u}; }
+inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u, 0u, 0u}; }
 
 // ---- scan (ssd_scan.cu) ----
 constexpr int kMaxBatch = SSD_MAX_ROUTERS;
@@ -305,8 +306,9 @@ cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, unsigned long lo
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.
 // `view`: the regained sketch's view; hosts outside its group are not listed.
+// tensor_pairs: the pair level on the tensor cores when eta is a multiple of 128 and pruning is on.
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
                                unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches,
-                               uint32_t view = 0);
+                               uint32_t view = 0, bool tensor_pairs = false);
 
 }  // namespace ssd

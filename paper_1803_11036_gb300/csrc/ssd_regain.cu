@@ -5,9 +5,11 @@
 //   is kept only when the union of its two estimators still has R_k >= the
 //   threshold: the union is an elementwise maximum, so R_k = popcount of the
 //   AND of the "recorder < k" bitmaps, and it can only fall as rows are added;
-//   a dropped tuple would fail the final test. Computed as 64 x 64 tiles of
-//   AND-popcounts (4 x 4 per thread, one carry-save step per two words) with
-//   the bitmaps staged in shared memory and one append per tile.
+//   a dropped tuple would fail the final test. Computed either as an fp8 GEMM of
+//   the bitmaps expanded to bytes on the tensor cores (k_pairs_tc, the default
+//   for eta a multiple of 128), or as 64 x 64 tiles of AND-popcounts on the CUDA
+//   cores (4 x 4 per thread, one carry-save step per two words) with the bitmaps
+//   staged in shared memory; one append per tile either way.
 // Level i >= 2: the overlap test fixes the low q-delta bits of he_i
 //   (B(i) mod 2^(q-delta) = B(i-1) >> delta with B(j) = he_0 XOR he_j), so the
 //   only row-i estimators a candidate can extend to are the hot ones with those
@@ -267,6 +269,274 @@ __global__ void __launch_bounds__(kBlock, 3) k_pairs(const Dims d, const Scratch
     }
     __syncthreads();   // wsum / tile_base are reused by the next tile
   }
+}
+
+// ---- the pair level on the tensor cores ----
+// R_k of the union of he_0 and he_1 is the popcount of the AND of their "recorder < k" bitmaps:
+// the dot product of the two bitmaps read as 0/1 vectors, so the whole pair level is one binary
+// matrix product. k_pairs_tc computes it as an fp8 GEMM on tcgen05: every bit becomes an e4m3
+// byte (1.0 or 0), A = the row-0 bitmaps (128 per tile), B = the row-1 bitmaps (256 per tile),
+// K = eta, accumulated in f32 in tensor memory. The result is exact: every sum is at most
+// eta <= 2^15 < 2^24. The bytes are expanded from the bitmaps straight into shared memory, 128
+// recorders per stage with two stages in flight (the next stage's words are loaded into
+// registers while the current one is expanded); one thread issues a stage's four MMAs and
+// commits them to the stage's mbarrier, which frees its buffer two stages later. The epilogue
+// reads the accumulator back (tcgen05.ld), applies the threshold and appends the kept pairs with
+// one atomic per tile, as k_pairs does. Waits are bounded: a wait that runs out marks the call
+// SSD_STATUS_INTERNAL, and the tile's memory is still released.
+constexpr uint32_t kTcM = 128, kTcN = 256, kTcKc = 128;   // tile rows of row 0 / of row 1; K bytes per stage
+constexpr uint32_t kTcThreads = 256;
+constexpr uint32_t kTcStageA = kTcM * kTcKc, kTcStageB = kTcN * kTcKc;
+constexpr uint32_t kTcSmem = 2 * (kTcStageA + kTcStageB) + 1024;   // two stages + alignment slack
+constexpr uint32_t kTcCols = 256;                                   // the 128 x 256 f32 accumulator
+constexpr uint32_t kTcItems = (kTcM + kTcN) * (kTcKc / 32) / kTcThreads;   // bitmap words per thread per stage
+constexpr long long kTcWaitCycles = 4000000000ll;                   // about two seconds of SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of (row, k byte) in a stage tile, the canonical K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes (128 contiguous bytes), 128 bytes apart along K (the
+// leading byte offset) and 8 x 128 = 1024 bytes apart along the rows (the stride byte offset).
+__device__ __forceinline__ uint32_t tc_off(uint32_t row, uint32_t kbyte) {
+  return (row >> 3) * 1024u + (kbyte >> 4) * 128u + (row & 7u) * 16u + (kbyte & 15u);
+}
+
+// Shared-memory matrix descriptor for that layout: start address, leading and stride byte
+// offsets (each >> 4), the fixed 0b001 at bits 46-48, base offset 0, no swizzle (bits 61-63).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor of kind::f8f6f4: D in f32 (bits 4-5 = 1), A and B e4m3 (bits 7-9 and
+// 10-12 = 0), both K-major (bits 15 and 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | ((kTcN >> 3) << 17) | ((kTcM >> 4) << 24);
+
+// 32 bits of a bitmap as 32 e4m3 bytes in bit order: 1.0 (0x38) for a set bit, 0 otherwise.
+// x * 0x00204081 = x + (x << 7) + (x << 14) + (x << 21) moves bit i of a nibble x to bit 8i (the
+// four copies do not overlap, so nothing carries); & 0x01010101 keeps those bits, and the
+// multiply by 0x38 turns each into the byte 0x38.
+__device__ __forceinline__ uint32_t nib_bytes(uint32_t nib) { return ((nib * 0x00204081u) & 0x01010101u) * 0x38u; }
+__device__ __forceinline__ void expand32(uint32_t w, uint4& lo, uint4& hi) {
+  lo = make_uint4(nib_bytes(w & 15u), nib_bytes((w >> 4) & 15u), nib_bytes((w >> 8) & 15u), nib_bytes((w >> 12) & 15u));
+  hi = make_uint4(nib_bytes((w >> 16) & 15u), nib_bytes((w >> 20) & 15u), nib_bytes((w >> 24) & 15u),
+                  nib_bytes(w >> 28));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+// Waits for the phase of `parity` to complete; false when about two seconds pass first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const uint32_t a = smem_addr(b);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kTcWaitCycles) return false;
+  }
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+// The MMAs issued so far by this thread arrive on `bar` when they complete.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+// 32 consecutive accumulator columns of this warp's 32 lanes (one row per lane), waited for.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Blocks [0, tile_blocks) take the 128 x 256 tiles of HSE(0) x HSE(1) in turn (block b: tiles
+// b, b + tile_blocks, ...), with one tensor-memory allocation for all of them; with the bucket
+// index, block tile_blocks + m builds the buckets of row 2 + m (as in k_pairs). Needs eta a
+// multiple of 128 and pruning on (the caller checks).
+__global__ void __launch_bounds__(kTcThreads, 1) k_pairs_tc(const Dims d, const Scratch s, uint32_t tile_blocks) {
+  pdl_enter();
+  if (blockIdx.x >= tile_blocks) {
+    build_buckets(d, s, 2 + (blockIdx.x - tile_blocks));
+    return;
+  }
+  const uint32_t n0 = min(s.counters->hot[0], d.hse_cap);
+  const uint32_t n1 = min(s.counters->hot[1], d.hse_cap);
+  const uint32_t tn = (n1 + kTcN - 1) / kTcN;
+  const uint32_t ntiles = ((n0 + kTcM - 1) / kTcM) * tn;
+  if (blockIdx.x >= ntiles) return;   // block-uniform: nothing allocated yet
+  extern __shared__ uint8_t tc_raw[];
+  __shared__ __align__(8) uint64_t bar[3];   // stage buffer 0, stage buffer 1, a tile's MMAs done
+  __shared__ uint32_t tmem_base;
+  __shared__ uint32_t wsum[kTcThreads / 32];
+  __shared__ unsigned long long tile_base;
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* const sA[2] = {sm, sm + kTcStageA};
+  uint8_t* const sB[2] = {sm + 2 * kTcStageA, sm + 2 * kTcStageA + kTcStageB};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    mbar_init(&bar[2]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t* bmA = s.pool_bm;
+  const uint32_t* bmB = s.pool_bm + (uint64_t)d.hse_cap * d.words;
+  const uint32_t stages = d.words / 4;   // 128 recorders per stage
+  const uint32_t qr = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
+  const float thr = (float)d.thr;
+  uint32_t g = 0;        // stages issued by this block so far, over all its tiles
+  uint32_t tiles = 0;    // tiles finished by this block
+  bool ok = true;
+  for (uint32_t t = blockIdx.x; t < ntiles && ok; t += tile_blocks, ++tiles) {
+    const uint32_t m0 = (t / tn) * kTcM, c0 = (t % tn) * kTcN;
+    // this thread's bitmap words of a stage: item threadIdx.x + 256 u, row = item / 4, word = item % 4
+    auto load_stage = [&](uint32_t st, uint32_t (&w)[kTcItems]) {
+#pragma unroll
+      for (uint32_t u = 0; u < kTcItems; ++u) {
+        const uint32_t item = threadIdx.x + u * kTcThreads, row = item >> 2, q = item & 3u;
+        w[u] = 0;
+        if (row < kTcM) {
+          if (m0 + row < n0) w[u] = bmA[(uint64_t)(m0 + row) * d.words + st * 4 + q];
+        } else if (c0 + row - kTcM < n1) {
+          w[u] = bmB[(uint64_t)(c0 + row - kTcM) * d.words + st * 4 + q];
+        }
+      }
+    };
+    uint32_t cur[kTcItems], nxt[kTcItems];
+    load_stage(0, cur);
+    for (uint32_t st = 0; st < stages; ++st, ++g) {
+      const uint32_t b = g & 1u;
+      if (st + 1 < stages) load_stage(st + 1, nxt);
+      // the MMAs of this block's stage g - 2 have read this buffer
+      const bool free_ = g < 2 || mbar_wait(&bar[b], ((g - 2) >> 1) & 1u);
+      if (!__syncthreads_and(free_)) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kTcItems; ++u) {
+        const uint32_t item = threadIdx.x + u * kTcThreads, row = item >> 2, q = item & 3u;
+        uint8_t* tile = row < kTcM ? sA[b] : sB[b];
+        const uint32_t rr = row < kTcM ? row : row - kTcM;
+        uint4 lo, hi;
+        expand32(cur[u], lo, hi);
+        *reinterpret_cast<uint4*>(tile + tc_off(rr, q * 32)) = lo;
+        *reinterpret_cast<uint4*>(tile + tc_off(rr, q * 32 + 16)) = hi;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stores, visible to the MMAs
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_addr(sA[b]), b0 = smem_addr(sB[b]);
+#pragma unroll
+        for (uint32_t j = 0; j < kTcKc / 32; ++j)   // K = 32 bytes per MMA: two core matrices along K
+          tc_mma(tmem, tc_desc(a0 + j * 256u), tc_desc(b0 + j * 256u), (st | j) != 0);
+        tc_commit(&bar[b]);
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kTcItems; ++u) cur[u] = nxt[u];
+    }
+    if (!ok) break;
+    if (threadIdx.x == 0) tc_commit(&bar[2]);   // this tile's MMAs, done
+    if (!__syncthreads_and(mbar_wait(&bar[2], tiles & 1u))) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows of the tile), columns 128 (w / 4) .. +127
+    uint32_t masks[4];
+    uint32_t mine = 0;
+    const uint32_t ia = m0 + qr * 32 + lane;
+#pragma unroll
+    for (uint32_t cc = 0; cc < 4; ++cc) {
+      const uint32_t col = half * 128 + cc * 32;
+      uint32_t v[32];
+      tc_ld32(tmem + ((qr * 32u) << 16) + col, v);
+      uint32_t m = 0;
+#pragma unroll
+      for (uint32_t j = 0; j < 32; ++j)
+        if (ia < n0 && c0 + col + j < n1 && __uint_as_float(v[j]) >= thr) m |= 1u << j;
+      masks[cc] = m;
+      mine += __popc(m);
+    }
+    // the accumulator has been read: the next tile's first MMA may overwrite it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kTcThreads / 32; ++w) {
+        const uint32_t x = wsum[w];
+        wsum[w] = run;
+        run += x;
+      }
+      tile_base = run ? atomicAdd(&s.counters->level[1], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = tile_base + wsum[warp] + (incl - mine);
+#pragma unroll
+    for (uint32_t cc = 0; cc < 4; ++cc) {
+      uint32_t m = masks[cc];
+      while (m) {
+        const uint32_t j = __ffs(m) - 1;
+        m &= m - 1;
+        if (pos < d.ctb_cap) {
+          s.ctb[0][pos * d.r + 0] = ia;
+          s.ctb[0][pos * d.r + 1] = c0 + half * 128 + cc * 32 + j;
+        } else {
+          atomicOr(&s.counters->status, SSD_STATUS_CTB_OVERFLOW);
+        }
+        ++pos;
+      }
+    }
+    __syncthreads();   // wsum and tile_base are reused by the next tile
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(&s.counters->status, SSD_STATUS_INTERNAL);
+      tc_commit(&bar[2]);   // then wait (bounded) for what is still in flight before releasing
+    }
+    __syncthreads();
+    mbar_wait(&bar[2], tiles & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // Popcount of the AND of the "recorder < k" bitmaps of tuple tl (rows 0..i-1)
@@ -566,10 +836,11 @@ __global__ void __launch_bounds__(kListThreads) k_list(const Dims d, const Scrat
 
 cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, uint32_t* rk, uint64_t cap,
                                unsigned long long* n_out_dev, int sms, cudaStream_t st, int* launches,
-                               uint32_t view) {
-  // k_list's dynamic shared memory limit and k_pairs' occupancy, once per device
+                               uint32_t view, bool tensor_pairs) {
+  // k_list's and k_pairs_tc's dynamic shared memory limits and k_pairs' occupancy, once per device
   constexpr int kDevices = 64;
   static bool attr[kDevices] = {};
+  static bool tc_attr[kDevices] = {};
   static int pair_bps_of[kDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -587,9 +858,19 @@ cudaError_t launch_regain_tail(const Dims& d, const Scratch& s, uint32_t* ips, u
     if (e != cudaSuccess) return e;
     if (pair_bps < 1) pair_bps = 1;
   }
-  const uint32_t pair_blocks = (uint32_t)(sms * pair_bps);
   const uint32_t bucket_blocks = s.bucket_off && d.r > 2 ? d.r - 2 : 0;
-  e = launch_pdl(k_pairs, pair_blocks + bucket_blocks, kBlock, 0, st, d, s, pair_blocks);
+  if (tensor_pairs && !(d.flags & SSD_NO_PRUNE) && (d.words & 3u) == 0) {
+    if (!tc_attr[dev]) {
+      e = cudaFuncSetAttribute(k_pairs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+      if (e != cudaSuccess) return e;
+      tc_attr[dev] = true;
+    }
+    const uint32_t tile_blocks = (uint32_t)sms;   // one resident block per SM (registers); each loops over tiles
+    e = launch_pdl(k_pairs_tc, tile_blocks + bucket_blocks, kTcThreads, kTcSmem, st, d, s, tile_blocks);
+  } else {
+    const uint32_t pair_blocks = (uint32_t)(sms * pair_bps);
+    e = launch_pdl(k_pairs, pair_blocks + bucket_blocks, kBlock, 0, st, d, s, pair_blocks);
+  }
   if (e != cudaSuccess) return e;
   *launches += 1;
   for (uint32_t i = 2; i < d.r; ++i) {

@@ -16,15 +16,15 @@ pytestmark = pytest.mark.gpu
 
 TUNINGS = [
     dict(touch_chunk_bytes=2 << 20, stream_blocks_per_sm=1, scan_blocks_per_sm=2, scan_unroll=1, merge_group=2,
-         combine_touches=1, collect_touches=0),
+         combine_touches=1, collect_touches=0, pair_level=1),
     dict(touch_chunk_bytes=4 << 20, stream_blocks_per_sm=2, scan_blocks_per_sm=32, scan_unroll=8, merge_group=4,
-         combine_touches=1, collect_touches=1),
+         combine_touches=1, collect_touches=1, pair_level=0),
     dict(touch_chunk_bytes=16 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=1, scan_unroll=2, merge_group=8,
-         combine_touches=0, collect_touches=1),
+         combine_touches=0, collect_touches=1, pair_level=1),
     dict(touch_chunk_bytes=8 << 20, stream_blocks_per_sm=3, scan_blocks_per_sm=4, scan_unroll=4, merge_group=8,
-         combine_touches=2, collect_touches=0),
+         combine_touches=2, collect_touches=0, pair_level=0),
     dict(touch_chunk_bytes=2 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=8, scan_unroll=4, merge_group=8,
-         combine_touches=2, collect_touches=1),
+         combine_touches=2, collect_touches=1, pair_level=0),
 ]
 
 
@@ -75,9 +75,9 @@ def test_tuning_rejects_bad_values():
     ctx = ssd.Context(ssd.make_params(W["params"]), tg.hash_tables(W["hash_seed"]))
     before = ctx.tuning
     assert before == dict(touch_chunk_bytes=32 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=8, scan_unroll=4,
-                          merge_group=8, combine_touches=0, collect_touches=0)
+                          merge_group=8, combine_touches=0, collect_touches=0, pair_level=0)
     for bad in (dict(scan_unroll=3), dict(merge_group=1), dict(scan_blocks_per_sm=0), dict(scan_blocks_per_sm=33),
-                dict(stream_blocks_per_sm=9), dict(combine_touches=3), dict(collect_touches=2),
+                dict(stream_blocks_per_sm=9), dict(combine_touches=3), dict(collect_touches=2), dict(pair_level=2),
                 dict(touch_chunk_bytes=1 << 10),
                 dict(touch_chunk_bytes=2 << 30)):
         with pytest.raises(ssd.SSDError) as e:

@@ -11,7 +11,7 @@ from paper_1803_11036_gb300._abi import TUNING_FIELDS
 
 P = dict(log2_eta=11, q=18, r=5, delta=5, k=60, theta=1024)
 T = dict(touch_chunk_bytes=32 << 20, stream_blocks_per_sm=0, scan_blocks_per_sm=8, scan_unroll=4, merge_group=8,
-         combine_touches=0, collect_touches=0)
+         combine_touches=0, collect_touches=0, pair_level=0)
 
 
 def test_key_separates_device_params_routers_and_size():
