@@ -294,34 +294,37 @@ def step_rooflines(pk, scan_ms, scan_pk, slot_pass, slot_tail, close_pass, close
 
 # ---------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(W: dict):
-    """A bounded sample of the workload for the single-threaded oracle: the same recipe with
-    2^4 fewer columns and 2^4 fewer packets per slot, which keeps the recorder bytes per packet
+def oracle_sample(W: dict, scale_log2: int = 0):
+    """The workload for the single-threaded oracle: the same recipe, or (scale_log2 = s > 0) with
+    2^s fewer columns and 2^s fewer packets per slot, which keeps the recorder bytes per packet
     (the advance and merge passes) equal to the full workload's."""
     import trafficgen as tg
     S = tg.workload(W["_name"]) if "_name" in W else W
     S = json.loads(json.dumps(S))
+    name = W.get("_name", "workload")
+    if not scale_log2:
+        prm = S["params"]
+        return S, (f"{name} as timed (q={prm['q']}, {S['traffic'].get('count_a')} packets/slot/router); "
+                   f"advance+scan+merge+regain per slot, window starting empty")
     prm = S["params"]
-    q = prm["q"] - 4
+    q = prm["q"] - scale_log2
     r = prm["r"]
     delta = max(1, -(-(32 - q) // (r - 2)))
     prm.update(q=q, delta=delta)
     tr = S["traffic"]
-    if tr.get("count") == "fixed":
-        tr["count_a"] = max(1, tr["count_a"] >> 4)
-    elif tr.get("count") == "split":
-        tr["count_a"] = max(1, tr["count_a"] >> 4)
-    tr["n_src"] = max(1, tr["n_src"] >> 4)
-    desc = (f"{W.get('_name', 'workload')} recipe at 1/16 scale: q={q}, delta={delta}, "
+    if tr.get("count") in ("fixed", "split"):
+        tr["count_a"] = max(1, tr["count_a"] >> scale_log2)
+    tr["n_src"] = max(1, tr["n_src"] >> scale_log2)
+    desc = (f"{name} recipe at 1/{1 << scale_log2} scale: q={q}, delta={delta}, "
             f"{tr.get('count_a')} packets/slot/router, {tr['n_src']} sources; advance+scan+merge+regain per slot")
     return S, desc
 
 
 class OracleSlots:
-    def __init__(self, W: dict):
+    def __init__(self, W: dict, scale_log2: int = 0):
         import oracle
         import trafficgen as tg
-        S, self.desc = oracle_sample(W)
+        S, self.desc = oracle_sample(W, scale_log2)
         self.p = oracle.params(S["params"])
         self.tabs = tg.hash_tables(S["hash_seed"])
         self.T = tg.Traffic(**S["traffic"])
@@ -336,6 +339,8 @@ class OracleSlots:
 
 
 def cpu_baseline(W: dict, budget_s: float = 12.0, min_slots: int = 3) -> dict:
+    """The oracle, as it stands, on the bench's own workload: slots until `budget_s` has passed
+    (at least min_slots), the window starting empty."""
     o = OracleSlots(W)
     pk, slots = 0, 0
     t0 = time.perf_counter()
@@ -349,7 +354,10 @@ def cpu_baseline(W: dict, budget_s: float = 12.0, min_slots: int = 3) -> dict:
 
 
 def run_reference(args, world, rank):
-    """The oracle, as it stands, as the reference arm (rank 0 only)."""
+    """The oracle, as it stands, as the reference arm (rank 0 only), on the same workload and
+    metric as our arm: warm-up slots, then `steps` timed slots of the same traffic, the window
+    starting empty (the oracle's cost per slot is its advance, merge and hot-estimator passes over
+    the whole RSEA plus the scan, whatever the window holds)."""
     if rank != 0:
         return
     import trafficgen as tg
