@@ -247,14 +247,17 @@ def traced(ctx, stream, calls):
     return [e[0].elapsed_time(e[1]) for e in E], [e[1].elapsed_time(e[2]) for e in E]
 
 
-def step_rooflines(pk, scan_ms, scan_pk, slot_pass, slot_tail, close_pass, close_tail, pass_bytes, r, peak):
+def step_rooflines(pk, scan_ms, scan_pk, slot_pass, slot_tail, close_pass, close_tail, rec_bytes, r, peak):
     """Each step of the slot against its own roofline (algorithmic bytes / time / measured HBM).
-    scan: 8 B pair read + r x 2 B recorder writes per packet; streaming passes: 4 B per recorder
-    (2 read + 2 written) per router; the candidate levels and the list are latency-bound (a few
-    MB of bitmaps in L2 per slot), so only their time is given."""
+    scan: 8 B pair read + r x 2 B recorder writes per packet (Algorithm 2); streaming pass: every
+    recorder of every router read once, 2 B (rec_bytes), since with stamp recorders the advance
+    writes nothing but the recorders that reach distance 65535; the slot's pass adds the scan's
+    bytes; the candidate levels and the list are latency-bound (a few MB of bitmaps in L2 per
+    slot), so only their time is given."""
     scan_b = 8 + 2 * r
     sp, cp = statistics.mean(slot_pass), statistics.mean(close_pass)
     marginal = sp - cp
+    pass_bytes = rec_bytes + scan_b * pk
     def frac(b, ms):
         return None if ms <= 0 else round(b / (ms / 1e3) / 1e9 / peak, 4)
     def gbs(b, ms):
@@ -273,14 +276,17 @@ def step_rooflines(pk, scan_ms, scan_pk, slot_pass, slot_tail, close_pass, close
             "bound": "l2 atomics (touch bits)", "frac": frac(scan_b * pk, marginal),
             "target_frac": 0.5, "target_met": bool(marginal > 0 and scan_b * pk / (marginal / 1e3) / 1e9 >= 0.5 * peak)},
         "slot_pass": {
-            "what": "streaming pass of ssd_slot with the scan inside (pre-hash, chunk 0's touches, chunk "
-                    "launches: touches applied, hot extraction, advance, next chunk's touches)",
-            "ms_per_slice": round(sp, 4), "algorithmic_bytes": pass_bytes, "achieved_gbs": gbs(pass_bytes, sp),
-            "bound": "hbm", "frac": frac(pass_bytes, sp)},
+            "what": "streaming pass of ssd_slot with the scan inside (touch lists, chunk launches: touches "
+                    "applied, hot extraction, advance, next chunk's touches)",
+            "ms_per_slice": round(sp, 4), "algorithmic_bytes": pass_bytes,
+            "algorithmic_bytes_model": "2 B read per recorder + 18 B per packet (8 B pair read + r x 2 B "
+                                       "recorder writes)",
+            "achieved_gbs": gbs(pass_bytes, sp), "bound": "hbm", "frac": frac(pass_bytes, sp)},
         "close_pass": {
             "what": "ssd_close_slot's streaming pass with no scan (merge, hot extraction, advance: one launch)",
-            "ms_per_slice": round(cp, 4), "algorithmic_bytes": pass_bytes, "achieved_gbs": gbs(pass_bytes, cp),
-            "bound": "hbm", "frac": frac(pass_bytes, cp)},
+            "ms_per_slice": round(cp, 4), "algorithmic_bytes": rec_bytes,
+            "algorithmic_bytes_model": "2 B read per recorder",
+            "achieved_gbs": gbs(rec_bytes, cp), "bound": "hbm", "frac": frac(rec_bytes, cp)},
         "regain_tail": {
             "what": "pair level, row levels, final test and the sorted list (five launches)",
             "ms_per_slice": round(statistics.mean(slot_tail), 4),
@@ -522,7 +528,7 @@ def paper_c1_leg(rank: int, local: int, warmup: int = 3, steps: int = 30) -> dic
     scan_ms = sa.elapsed_time(sb) / len(tr)
     steps_ = step_rooflines(pk=statistics.mean(pk[t] for t in tr), scan_ms=scan_ms,
                             scan_pk=statistics.mean(pk[t] for t in tr), slot_pass=slot_pass, slot_tail=slot_tail,
-                            close_pass=close_pass, close_tail=close_tail, pass_bytes=eta * C * r * 4, r=r, peak=peak)
+                            close_pass=close_pass, close_tail=close_tail, rec_bytes=eta * C * r * 2, r=r, peak=peak)
     ctx.close()
     torch.cuda.empty_cache()
     mpps = timed / (ms * steps / 1e3) / 1e6
@@ -771,7 +777,7 @@ def run_ours(args, world, rank, local):
 
     eta, C, r = 1 << prm["log2_eta"], 1 << prm["q"], prm["r"]
     recorders = eta * C * r
-    pass_bytes = recorders * 2 * 2 * R          # each router's recorders read once and written once
+    rec_bytes = recorders * 2 * R               # each router's recorders read once (stamps: no advance writes)
     # the pass runs as chunk launches of `chunk` estimators (the tuned touch bits per chunk)
     n_se = r * C
     chunk = 1
@@ -782,7 +788,7 @@ def run_ours(args, world, rank, local):
     traffic = profiled_traffic(args.workload, chunk)
     steps = step_rooflines(pk=tr_pk, scan_ms=scan_ms, scan_pk=timed_pk / args.steps, slot_pass=slot_pass,
                            slot_tail=slot_tail, close_pass=close_pass, close_tail=close_tail,
-                           pass_bytes=pass_bytes, r=r, peak=peak)
+                           rec_bytes=rec_bytes, r=r, peak=peak)
     achieved = steps["slot_pass"]["achieved_gbs"]
 
     # ---- end to end through the C ABI from pinned host memory: ssd_slot_host copies each
@@ -899,13 +905,14 @@ def run_ours(args, world, rank, local):
         "batched_vs_plain": bvp,
         "batched_vs_plain_stress": stress,
         "served": served,
-        "roofline": {"kernel": "the streaming pass of ssd_slot: k_prehash, chunk 0's k_touch_packed and the "
-                               "k_chunk launches (the scan's touches applied, hot extraction, advance; the next "
-                               "chunk's touches collected in L2 between estimators)",
-                     "launches_per_pass": n_chunks, "algorithmic_bytes_per_chunk_launch": chunk * eta * 4 * R,
+        "roofline": {"kernel": "the streaming pass of ssd_slot: k_lists (every pair hashed once, touch lists "
+                               "per chunk) and the k_chunk launches (the scan's touches applied, hot extraction, "
+                               "advance; the next chunk's touches set in L2 between estimators)",
+                     "launches_per_pass": n_chunks + 1,
+                     "algorithmic_bytes_per_chunk_launch": chunk * eta * 2 * R,
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": steps["slot_pass"]["frac"], "peak_source": peak_kind,
-                     "algorithmic_bytes_per_pass": pass_bytes,
+                     "algorithmic_bytes_per_pass": steps["slot_pass"]["algorithmic_bytes"],
                      "traffic": traffic,
                      "traffic_source": None if traffic is None else
                      f"profiles/chunk_pass_{args.workload}.md (ncu DRAM bytes of one chunk launch)"},

@@ -24,6 +24,17 @@
  *  - A sketch is r rows x 2^q columns of sliding estimators, each eta = 2^log2_eta
  *    uint16 distance recorders, stored row-major: recorder j of estimator
  *    (row, col) is element ((row * 2^q) + col) * eta + j (Sec. 3.3).
+ *  - Wherever recorders cross this ABI (ssd_sketch_export, ssd_sketch_import,
+ *    ssd_regain_static, ssd_min_merge) they are the paper's distances: 0..65534
+ *    slots since a pair last set the recorder, 65535 for never or for 65535 slots
+ *    or more (Sec. 3.2). Inside a sketch the library stores each one as a stamp,
+ *    the slot counter modulo 65535 when a pair last set it (0xFFFF for distance
+ *    65535), next to the sketch's clock (its slot counter modulo 65535) in
+ *    device memory: the advance of every recorder by one is then the clock's
+ *    tick, and a slot writes only the recorders its pairs set (and, once in
+ *    65535 slots, those whose distance reaches 65535). Distances are a pure
+ *    function of the stamps and the clock, so every count, list and exported
+ *    array is that of the paper's recorders. ssd_sketch_data exposes the stamps.
  */
 #ifndef SSD_H
 #define SSD_H
@@ -147,8 +158,10 @@ SSD_API void ssd_sketch_destroy(ssd_sketch* s);
 SSD_API uint64_t ssd_sketch_bytes(const ssd_ctx* ctx);
 /* Slots the sketch has advanced since creation or import. */
 SSD_API int ssd_sketch_slot(const ssd_sketch* s, uint64_t* slot);
-/* Set the slot counter (host bookkeeping only, no GPU work): after replaying a
- * captured slot the caller advances the counters the replay cannot. */
+/* Set the host's slot counter (host bookkeeping only, no GPU work): after
+ * replaying a captured slot the caller advances the counters the replay cannot.
+ * The device clock the stamps refer to is moved on by the advancing calls
+ * themselves (and by their replays), never by this call. */
 SSD_API int ssd_sketch_set_slot(ssd_sketch* s, uint64_t slot);
 /* What a sketch counts (its view). Sec. 3.1 defines sliding super points for
  * the hosts of CNet, the first field of each pair, and obtains those of ONet by
@@ -179,11 +192,14 @@ SSD_API int ssd_sketch_view(const ssd_sketch* s, uint32_t* side, uint32_t* group
  * hosts its columns hold, the realised column load. Reads the whole RSEA once
  * and waits for `stream`. */
 SSD_API int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream);
-/* The device address of the sketch's recorders (ssd_sketch_bytes bytes, laid
- * out as described at the top of this file), owned by the library and valid
- * until the sketch is destroyed. For moving a sketch between GPUs without a
- * copy through the host (a collective library reads or writes it in place);
- * the caller orders such access against the context's stream. */
+/* The device address of the sketch's stored recorders (ssd_sketch_bytes bytes,
+ * laid out as described at the top of this file, in the stamp form: not
+ * distances), owned by the library and valid until the sketch is destroyed; the
+ * sketch's clock (uint32, its slot counter modulo 65535) follows them. For
+ * inspecting or checkpointing the raw state in place; to move recorders between
+ * GPUs as distances, export them to device memory (ssd_sketch_export) and import
+ * them on the other side. The caller orders such access against the context's
+ * stream. */
 SSD_API int ssd_sketch_data(const ssd_sketch* s, uint16_t** d_recorders);
 /* The reduction of Algorithm 5 when the routers' RSEAs are spread over several
  * GPUs (the paper ships every monitor server's RSEA to one server, Sec. 4):
@@ -197,12 +213,15 @@ SSD_API int ssd_sketch_data(const ssd_sketch* s, uint16_t** d_recorders);
  * Asynchronous on `stream`. */
 SSD_API int ssd_min_merge(ssd_ctx* ctx, uint16_t* d_out, const uint16_t* const* d_in, int n, uint64_t count,
                           void* stream);
-/* Copy `count` recorders starting at recorder `first` to dst (host or device).
- * Waits for `stream` before returning. Checkpointing a sketch is
+/* Write the distances (Sec. 3.2) of `count` recorders starting at recorder
+ * `first` to dst (host or device; device memory is written by a kernel, host
+ * memory through a staging buffer the context allocates on first use, up to
+ * 32 MiB). Waits for `stream` before returning. Checkpointing a sketch is
  * export + ssd_sketch_slot; resuming is import. */
 SSD_API int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream);
-/* Overwrite the whole sketch from src (host or device; ssd_sketch_bytes bytes)
- * and set its slot counter. Waits for `stream` before returning. */
+/* Overwrite the whole sketch from the distances in src (host or device;
+ * ssd_sketch_bytes bytes) and set its slot counter (and clock) to `slot`. Waits
+ * for `stream` before returning. */
 SSD_API int ssd_sketch_import(ssd_sketch* s, const uint16_t* src, uint64_t slot, void* stream);
 
 /* Algorithm 2 for every pair of d_pairs[0 .. 2*n_pairs): DRidx = H1(oip); for
@@ -229,7 +248,9 @@ SSD_API int ssd_scan_batch(ssd_sketch* const* sketches, const uint32_t* const* d
                    int n, void* stream);
 
 /* Window advance (Sec. 3.2, Sec. 4.3): every recorder below 65535 of each of
- * the n sketches grows by one; each sketch's slot counter grows by one. */
+ * the n sketches grows by one; each sketch's slot counter grows by one. (One
+ * read pass stores 0xFFFF into the recorders whose distance reaches 65535, then
+ * the sketches' clocks tick; no other recorder is written.) */
 SSD_API int ssd_advance(ssd_sketch* const* sketches, int n, void* stream);
 
 /* Algorithm 5: global[x] = UnionSE of routers[0..n)[x] for every recorder x,

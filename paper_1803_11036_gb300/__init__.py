@@ -124,9 +124,10 @@ class Sketch:
         return [int(x) for x in out[: self.ctx.params.r]]
 
     def device_view(self):
-        """The sketch's recorders as a CUDA int16 tensor sharing the library's memory (no copy;
-        the 16-bit patterns are the uint16 recorders). Valid while the sketch lives; the caller
-        orders its use against the context's stream."""
+        """The sketch's stored recorders as a CUDA int16 tensor sharing the library's memory (no
+        copy): the library's stamp form (the slot of a recorder's last touch modulo 65535, or 0xFFFF
+        for distance 65535), not the distances; export() and export_device() give distances.
+        Valid while the sketch lives; the caller orders its use against the context's stream."""
         torch = _torch()
         ptr = ctypes.c_void_p()
         check(self.ctx.L.ssd_sketch_data(self._h, ctypes.byref(ptr)), "ssd_sketch_data")
@@ -138,8 +139,32 @@ class Sketch:
 
         return torch.as_tensor(_Recorders(), device=self.ctx.device)
 
+    def export_device(self, out=None, first: int = 0, count: int | None = None, stream=None):
+        """Distance recorders [first, first+count) written to a CUDA int16 tensor (`out`, or a new
+        one) on the sketch's device; waits for the stream."""
+        torch = _torch()
+        n = self.ctx.sketch_bytes // 2
+        count = n - first if count is None else count
+        if out is None:
+            out = torch.empty(count, dtype=torch.int16, device=self.ctx.device)
+        if out.numel() != count or out.element_size() != 2 or not out.is_contiguous() or out.device != self.ctx.device:
+            raise ValueError("out must be a contiguous 16-bit tensor of `count` elements on the sketch's device")
+        check(self.ctx.L.ssd_sketch_export(self._h, first, count, ctypes.c_void_p(out.data_ptr()),
+                                           _stream_handle(stream, self.ctx.device)), "ssd_sketch_export")
+        return out
+
+    def load_device(self, recorders, slot: int, stream=None) -> None:
+        """Overwrite every recorder from a CUDA 16-bit tensor of distances and set the slot counter."""
+        if recorders.numel() * recorders.element_size() != self.ctx.sketch_bytes or not recorders.is_contiguous():
+            raise ValueError("recorder tensor has the wrong size")
+        if recorders.device != self.ctx.device:
+            raise ValueError("recorder tensor is on another device")
+        check(self.ctx.L.ssd_sketch_import(self._h, ctypes.c_void_p(recorders.data_ptr()), slot,
+                                           _stream_handle(stream, self.ctx.device)), "ssd_sketch_import")
+
     def export(self, first: int = 0, count: int | None = None, stream=None) -> np.ndarray:
-        """Recorders [first, first+count) copied to a host uint16 array (waits for the stream)."""
+        """Distance recorders [first, first+count) copied to a host uint16 array (waits for the
+        stream)."""
         n = self.ctx.sketch_bytes // 2
         count = n - first if count is None else count
         out = np.empty(count, dtype=np.uint16)
@@ -152,7 +177,7 @@ class Sketch:
         return self.export(((row << self.ctx.params.q) + col) * eta, eta, stream)
 
     def load(self, recorders: np.ndarray, slot: int, stream=None) -> None:
-        """Overwrite every recorder from a host uint16 array and set the slot counter."""
+        """Overwrite every recorder from a host uint16 array of distances and set the slot counter."""
         a = np.ascontiguousarray(recorders, dtype=np.uint16)
         if a.nbytes != self.ctx.sketch_bytes:
             raise ValueError("recorder array has the wrong size")

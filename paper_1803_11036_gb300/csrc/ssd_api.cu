@@ -56,12 +56,16 @@ struct ssd_ctx {
   // buffers' allocations with their guard words (ctb[i] = ctb_alloc[i] + kGuardWords)
   unsigned int* dbg;
   uint32_t* ctb_alloc[2];
+  // staging of ssd_sketch_export / ssd_sketch_import through host memory (grown on first use)
+  uint16_t* xfer;
+  uint64_t xfer_count;
 };
 
 struct ssd_sketch {
   ssd_ctx* ctx;
   int device;
-  uint16_t* dr;
+  uint16_t* dr;    // stamp recorders (ssd_internal.cuh), r * 2^q * eta of them
+  uint32_t* tm;    // the sketch's clock, slot mod 65535, in device memory right after the recorders
   uint64_t slot;
   uint32_t view;   // ssd::view_pack(side, group bits, group)
 };
@@ -135,6 +139,7 @@ bool same_view(ssd_sketch* const* v, int n) {
 int add_job(ssd::ScanBatch& b, int j, const ssd_sketch* sk, const uint32_t* pairs, uint64_t n, uint64_t* prefix) {
   uint16_t* dr = sk->dr;
   b.view[j] = sk->view;
+  b.tm[j] = sk->tm;
   if (n && !pairs) return SSD_EINVAL;
   if (reinterpret_cast<uintptr_t>(pairs) & 7u) return SSD_EINVAL;
   const uint32_t* head = nullptr;
@@ -172,16 +177,65 @@ int scan_jobs(ssd_ctx* ctx, ssd::ScanBatch& b, uint64_t total_vec, bool any_edge
   return SSD_OK;
 }
 
-int stream_pass(ssd_ctx* ctx, ssd_sketch* const* routers, int n, uint16_t* global, int mode, cudaStream_t st) {
+int stream_pass(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* global, int mode, cudaStream_t st) {
   ssd::StreamArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = n;
-  for (int i = 0; i < n; ++i) a.routers[i] = routers[i]->dr;
-  a.global = global;
+  for (int i = 0; i < n; ++i) {
+    a.routers[i] = routers[i]->dr;
+    a.tm[i] = routers[i]->tm;
+  }
+  a.global = global ? global->dr : nullptr;
+  a.global_tm = global ? global->tm : nullptr;
   cudaError_t e = ssd::launch_stream(ctx->d, ctx->s, a, mode, ctx->sms, ctx->tn, st);
   if (e != cudaSuccess) return cuda_fail(e, "stream kernel");
   ctx->launches += 1;
   return SSD_OK;
+}
+
+// The clocks of advanced sketches move on by one slot, after every launch that reads them.
+int tick(ssd_ctx* ctx, ssd_sketch* const* sketches, int n, cudaStream_t st) {
+  ssd::TickArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  for (int i = 0; i < n; ++i) a.tm[i] = sketches[i]->tm;
+  cudaError_t e = ssd::launch_tick(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tick kernel");
+  ctx->launches += 1;
+  return SSD_OK;
+}
+
+// Every recorder at distance 65535 (kNever) and the clock at slot 0.
+cudaError_t reset_sketch(ssd_sketch* sk, uint64_t bytes, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(sk->dr, 0xFF, bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sk->tm, 0, sizeof(uint32_t), st);
+  return e;
+}
+
+// The export/import staging buffer of at least `count` recorders (at most 16 Mi), grown on demand.
+int xfer_buffer(ssd_ctx* ctx, uint64_t want) {
+  if (want > (1ull << 24)) want = 1ull << 24;
+  if (ctx->xfer && ctx->xfer_count >= want) return SSD_OK;
+  SSD_CUDA(cudaDeviceSynchronize());
+  cudaFree(ctx->xfer);
+  ctx->xfer = nullptr;
+  ctx->xfer_count = 0;
+  if (cudaMalloc(&ctx->xfer, want * 2) != cudaSuccess) {
+    cudaGetLastError();
+    return SSD_ENOMEM;
+  }
+  ctx->xfer_count = want;
+  return SSD_OK;
+}
+
+// Whether p is memory a kernel of ctx's device can address directly (device or managed memory).
+bool device_memory(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 int trace(ssd_ctx* ctx, cudaEvent_t ev, cudaStream_t st) {
@@ -240,6 +294,7 @@ void free_ctx(ssd_ctx* c) {
   cudaFree(c->bucket_cnt);
   cudaFree(c->bucket_ent);
   cudaFree(c->n_out);
+  cudaFree(c->xfer);
   delete c;
 }
 
@@ -409,13 +464,15 @@ int ssd_sketch_create(ssd_ctx* ctx, ssd_sketch** out) {
   s->view = 0;
   s->dr = nullptr;
   const uint64_t bytes = ssd_sketch_bytes(ctx);
-  if (cudaMalloc(&s->dr, bytes) != cudaSuccess) {
+  // the recorders, then the clock (256 bytes keep the allocation's tail aligned)
+  if (cudaMalloc(&s->dr, bytes + 256) != cudaSuccess) {
     cudaGetLastError();
     delete s;
     return SSD_ENOMEM;
   }
-  // every distance recorder starts at 65535 (Sec. 3.2)
-  cudaError_t e = cudaMemsetAsync(s->dr, 0xFF, bytes, 0);
+  s->tm = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(s->dr) + bytes);
+  // every distance recorder starts at 65535 (Sec. 3.2): kNever; the clock at slot 0
+  cudaError_t e = reset_sketch(s, bytes, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     cudaFree(s->dr);
@@ -470,7 +527,7 @@ int ssd_sketch_occupancy(const ssd_sketch* s, uint64_t* rk_sum, void* stream) {
   // context's one stream like a regain
   unsigned long long* acc = ctx->stage;
   SSD_CUDA(cudaMemsetAsync(acc, 0, SSD_MAX_R * sizeof(unsigned long long), st));
-  cudaError_t e = ssd::launch_occupancy(ctx->d, s->dr, acc, ctx->sms, st);
+  cudaError_t e = ssd::launch_occupancy(ctx->d, s->dr, s->tm, acc, ctx->sms, st);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy kernel");
   ctx->launches += 1;
   unsigned long long h[SSD_MAX_R];
@@ -503,20 +560,60 @@ int ssd_min_merge(ssd_ctx* ctx, uint16_t* d_out, const uint16_t* const* d_in, in
 
 int ssd_sketch_export(const ssd_sketch* s, uint64_t first, uint64_t count, uint16_t* dst, void* stream) {
   if (!s || (count && !dst)) return SSD_EINVAL;
-  const uint64_t n = ssd_sketch_bytes(s->ctx) / 2;
+  ssd_ctx* ctx = s->ctx;
+  const uint64_t n = ssd_sketch_bytes(ctx) / 2;
   if (first > n || count > n - first) return SSD_EINVAL;
   if (!count) return SSD_OK;
-  DeviceGuard g(s->ctx->device);
-  SSD_CUDA(cudaMemcpyAsync(dst, s->dr + first, count * 2, cudaMemcpyDefault, as_stream(stream)));
-  SSD_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  // the stamps read back as the distances of Sec. 3.2 at the sketch's clock
+  if (device_memory(dst)) {
+    cudaError_t e = ssd::launch_flip(s->dr + first, dst, count, s->tm, 0, nullptr, ctx->sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "export kernel");
+    ctx->launches += 1;
+  } else {
+    int rc = xfer_buffer(ctx, count);
+    if (rc != SSD_OK) return rc;
+    for (uint64_t done = 0; done < count;) {
+      const uint64_t m = count - done < ctx->xfer_count ? count - done : ctx->xfer_count;
+      cudaError_t e = ssd::launch_flip(s->dr + first + done, ctx->xfer, m, s->tm, 0, nullptr, ctx->sms, st);
+      if (e != cudaSuccess) return cuda_fail(e, "export kernel");
+      ctx->launches += 1;
+      SSD_CUDA(cudaMemcpyAsync(dst + done, ctx->xfer, m * 2, cudaMemcpyDeviceToHost, st));
+      SSD_CUDA(cudaStreamSynchronize(st));   // the staging buffer is reused by the next piece
+      done += m;
+    }
+  }
+  SSD_CUDA(cudaStreamSynchronize(st));
   return SSD_OK;
 }
 
 int ssd_sketch_import(ssd_sketch* s, const uint16_t* src, uint64_t slot, void* stream) {
   if (!s || !src) return SSD_EINVAL;
-  DeviceGuard g(s->ctx->device);
-  SSD_CUDA(cudaMemcpyAsync(s->dr, src, ssd_sketch_bytes(s->ctx), cudaMemcpyDefault, as_stream(stream)));
-  SSD_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  ssd_ctx* ctx = s->ctx;
+  const uint64_t n = ssd_sketch_bytes(ctx) / 2;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  // distances to stamps at the clock of `slot`; the clock is stored with the first piece
+  const uint32_t tm = (uint32_t)(slot % 65535u);
+  if (device_memory(src)) {
+    cudaError_t e = ssd::launch_flip(src, s->dr, n, nullptr, tm, s->tm, ctx->sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "import kernel");
+    ctx->launches += 1;
+  } else {
+    int rc = xfer_buffer(ctx, n);
+    if (rc != SSD_OK) return rc;
+    for (uint64_t done = 0; done < n;) {
+      const uint64_t m = n - done < ctx->xfer_count ? n - done : ctx->xfer_count;
+      SSD_CUDA(cudaMemcpyAsync(ctx->xfer, src + done, m * 2, cudaMemcpyHostToDevice, st));
+      cudaError_t e = ssd::launch_flip(ctx->xfer, s->dr + done, m, nullptr, tm, done ? nullptr : s->tm, ctx->sms, st);
+      if (e != cudaSuccess) return cuda_fail(e, "import kernel");
+      ctx->launches += 1;
+      SSD_CUDA(cudaStreamSynchronize(st));   // the staging buffer is reused by the next piece
+      done += m;
+    }
+  }
+  SSD_CUDA(cudaStreamSynchronize(st));
   s->slot = slot;
   return SSD_OK;
 }
@@ -598,6 +695,7 @@ int ssd_advance(ssd_sketch* const* sketches, int n, void* stream) {
   if (!same_ctx(sketches, n, &ctx)) return SSD_EINVAL;
   DeviceGuard g(ctx->device);
   int rc = stream_pass(ctx, sketches, n, nullptr, ssd::kAdvance, as_stream(stream));
+  if (rc == SSD_OK) rc = tick(ctx, sketches, n, as_stream(stream));
   if (rc != SSD_OK) return rc;
   for (int i = 0; i < n; ++i) sketches[i]->slot += 1;
   return SSD_OK;
@@ -612,7 +710,7 @@ int ssd_merge(ssd_sketch* const* routers, int n, ssd_sketch* global, void* strea
     if (routers[i]->slot != routers[0]->slot) return SSD_ESTATE;
   }
   DeviceGuard g(ctx->device);
-  int rc = stream_pass(ctx, routers, n, global->dr, 0, as_stream(stream));
+  int rc = stream_pass(ctx, routers, n, global, 0, as_stream(stream));
   if (rc != SSD_OK) return rc;
   global->slot = routers[0]->slot;
   global->view = routers[0]->view;
@@ -659,10 +757,11 @@ int ssd_close_slot(ssd_ctx* ctx, ssd_sketch* const* routers, int n, ssd_sketch* 
   SSD_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(ssd::DevCounters), st));
   int rc = trace(ctx, ctx->tr_start, st);
   if (rc != SSD_OK) return rc;
-  rc = stream_pass(ctx, routers, n, global ? global->dr : nullptr, ssd::kAdvance | ssd::kHot, st);
+  rc = stream_pass(ctx, routers, n, global, ssd::kAdvance | ssd::kHot, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
   if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, routers[0]->view);
+  if (rc == SSD_OK) rc = tick(ctx, routers, n, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   const uint64_t merged = routers[0]->slot;
@@ -770,7 +869,9 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   ssd::ChunkArgs a;
   std::memset(&a, 0, sizeof(a));
   a.router = router->dr;
+  a.tm = router->tm;
   a.global = global ? global->dr : nullptr;
+  a.global_tm = global ? global->tm : nullptr;
   a.view = router->view;
   cudaError_t e;
   if (lists) {
@@ -832,6 +933,7 @@ static int slot_chunks1(ssd_ctx* ctx, ssd_sketch* router, const uint32_t* pairs,
   rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
   if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, router->view);
+  if (rc == SSD_OK) rc = tick(ctx, &router, 1, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   if (global) {
@@ -891,8 +993,12 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   ssd::StreamArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = n;
-  for (int i = 0; i < n; ++i) a.routers[i] = routers[i]->dr;
+  for (int i = 0; i < n; ++i) {
+    a.routers[i] = routers[i]->dr;
+    a.tm[i] = routers[i]->tm;
+  }
   a.global = global ? global->dr : nullptr;
+  a.global_tm = global ? global->tm : nullptr;
   for (uint64_t c = 0; c < n_chunks; ++c) {
     const int bsel = (int)(c & 1);
     const uint64_t se0 = c * count;
@@ -914,6 +1020,7 @@ int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_
   rc = trace(ctx, ctx->tr_pass, st);
   unsigned long long* nd = d_n_out ? reinterpret_cast<unsigned long long*>(d_n_out) : ctx->n_out;
   if (rc == SSD_OK) rc = regain_after_pass(ctx, d_ips, d_rk, cap, nd, st, routers[0]->view);
+  if (rc == SSD_OK) rc = tick(ctx, routers, n, st);
   if (rc == SSD_OK) rc = trace(ctx, ctx->tr_end, st);
   if (rc != SSD_OK) return rc;
   const uint64_t merged = routers[0]->slot;
@@ -1225,7 +1332,7 @@ int ssd_autotune(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const
   for (int i = 0; i < n + 1 && e == cudaSuccess; ++i) {
     ssd_sketch* sk = i < n ? routers[i] : global;
     if (!sk) continue;
-    e = cudaMemsetAsync(sk->dr, 0xFF, bytes, st);
+    e = reset_sketch(sk, bytes, st);
     sk->slot = 0;
   }
   // the tuning slots ran with no list capacity: clear the status they left

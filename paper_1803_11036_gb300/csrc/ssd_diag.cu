@@ -8,20 +8,12 @@
 namespace ssd {
 namespace {
 
-// Recorders below k among the 8 in v (two per 32-bit word).
-__device__ __forceinline__ uint32_t below8(uint4 v, uint32_t k) {
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-  uint32_t c = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) c += ((w[i] & 0xFFFFu) < k) + ((w[i] >> 16) < k);
-  return c;
-}
-
 // Grid-stride over the RSEA's 16-byte vectors; a thread's count goes to its
 // block's row total when its row changes, the block's totals to rk_sum.
 __global__ void __launch_bounds__(kBlock) k_occupancy(const Dims d, const uint4* __restrict__ dr,
-                                                      unsigned long long* rk_sum) {
+                                                      const uint32_t* tm, unsigned long long* rk_sum) {
   __shared__ unsigned long long part[SSD_MAX_R];
+  const Clock c = make_clock(read_tm(tm), d.k);   // the recorders are stamps at this clock
   if (threadIdx.x < SSD_MAX_R) part[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t per_row = ((uint64_t)1 << (d.q + d.log2_eta)) >> 3;
@@ -36,7 +28,7 @@ __global__ void __launch_bounds__(kBlock) k_occupancy(const Dims d, const uint4*
       cnt = 0;
       row = rv;
     }
-    cnt += below8(__ldcs(dr + v), d.k);
+    cnt += __popc(win8(__ldcs(dr + v), c));   // the window test of the streaming passes
   }
   if (cnt) atomicAdd(&part[row], cnt);
   __syncthreads();
@@ -45,9 +37,9 @@ __global__ void __launch_bounds__(kBlock) k_occupancy(const Dims d, const uint4*
 
 }  // namespace
 
-cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, unsigned long long* rk_sum, int sms,
-                             cudaStream_t st) {
-  k_occupancy<<<sms * 8, kBlock, 0, st>>>(d, reinterpret_cast<const uint4*>(dr), rk_sum);
+cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, const uint32_t* tm, unsigned long long* rk_sum,
+                             int sms, cudaStream_t st) {
+  k_occupancy<<<sms * 8, kBlock, 0, st>>>(d, reinterpret_cast<const uint4*>(dr), tm, rk_sum);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,93 @@ struct Tuning {
 };
 inline Tuning default_tuning() { return Tuning{0u, 8u, 4u, 8u, 0u, 0u, 0u}; }
 
+// ---- stamp recorders ----
+// The library keeps each distance recorder of Sec. 3.2 as the slot of the last pair that set it to
+// 0, modulo 65535 (a stamp in 0..65534), or kNever (0xFFFF) when its distance is 65535: never set,
+// or not for 65535 slots. A sketch holds tm = its slot counter modulo 65535 in device memory, and
+// the distance of a recorder x is 65535 for x = kNever, (tm - x) mod 65535 otherwise. Algorithm 2
+// (set to 0) stores tm. The advance of Sec. 4.3 (every recorder + 1, saturating at 65535) is
+// tm + 1 together with kNever stored into the recorders whose distance reaches 65535, the stamp
+// tm + 1 mod 65535. So between those expiries a slot writes only the recorders a pair set; the
+// distances, and every R_k, hot estimator and list, are those of the paper's recorders, and an
+// exported sketch holds the distances themselves.
+constexpr uint32_t kNever = 0xFFFFu;
+__host__ __device__ __forceinline__ uint32_t tm_next(uint32_t tm) { return tm + 1u >= 65535u ? 0u : tm + 1u; }
+// Two recorders (one 32-bit word): distances from stamps at clock tm2 (tm in both halves), and
+// stamps from distances; the one map does both ways, kNever <-> 65535.
+__device__ __forceinline__ uint32_t flip2(uint32_t v, uint32_t tm2) {
+  return __vadd2(__vsub2(tm2, v), __vcmpgtu2(v, tm2)) | __vcmpeq2(v, 0xFFFFFFFFu);
+}
+__device__ __forceinline__ uint4 flip8(uint4 v, uint32_t tm2) {
+  return make_uint4(flip2(v.x, tm2), flip2(v.y, tm2), flip2(v.z, tm2), flip2(v.w, tm2));
+}
+// Per-launch constants of the window test and the expiry on stamps (make_clock). A recorder is
+// inside the window (distance < k) when (x - lo) mod 2^16 < klim and x is not kNever; the window
+// [lo, tm] of the 65535 stamps wraps past 65534 when tm < k - 1, and then kNever lies inside the
+// 16-bit range [lo, lo + k], so klim = k + 1 and kNever is excluded by `wrap`. Recorders holding
+// distances (the allocation-free regain's input) use lo = 0, klim = k.
+struct Clock {
+  uint32_t tm2;     // tm, both halves
+  uint32_t lo2;     // oldest stamp in the window, both halves
+  uint32_t klim2;   // length of the window's 16-bit range, both halves
+  uint32_t xe2;     // the stamp whose distance reaches 65535 at the advance, both halves
+  uint32_t wrap;    // kNever lies in the 16-bit range of the window
+};
+__host__ __device__ __forceinline__ Clock make_clock(uint32_t tm, uint32_t k) {
+  Clock c;
+  const bool wrap = tm + 1u < k;
+  const uint32_t lo = wrap ? tm + 65536u - k : tm + 1u - k;
+  const uint32_t klim = wrap ? k + 1u : k;
+  const uint32_t xe = tm_next(tm);
+  c.tm2 = tm | (tm << 16);
+  c.lo2 = lo | (lo << 16);
+  c.klim2 = klim | (klim << 16);
+  c.xe2 = xe | (xe << 16);
+  c.wrap = wrap ? 1u : 0u;
+  return c;
+}
+__host__ __device__ __forceinline__ Clock distance_clock(uint32_t k) {
+  Clock c;
+  c.tm2 = 0u;
+  c.lo2 = 0u;
+  c.klim2 = k | (k << 16);
+  c.xe2 = 0xFFFFFFFFu;   // never matched by a stored value that is advanced (no advance on distances)
+  c.wrap = 0u;
+  return c;
+}
+// 0xFFFF in each half of a word whose recorder lies inside the window.
+__device__ __forceinline__ uint32_t win2(uint32_t x, const Clock& c) {
+  uint32_t m = __vcmpltu2(__vsub2(x, c.lo2), c.klim2);
+  if (c.wrap) m &= ~__vcmpeq2(x, 0xFFFFFFFFu);
+  return m;
+}
+// Bit i = recorder i of the 8 in (m0, m1, m2, m3) has 0xFFFF: the high byte of each half gathered
+// by two byte permutes, each byte reduced to one bit, four bits summed into the top byte by one
+// multiply (the bits are distinct, so nothing carries).
+__device__ __forceinline__ uint32_t pack8(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
+  const uint32_t a = __byte_perm(m0, m1, 0x7531u), b = __byte_perm(m2, m3, 0x7531u);
+  return (((a & 0x08040201u) * 0x01010101u) >> 24) | (((b & 0x80402010u) * 0x01010101u) >> 24);
+}
+__device__ __forceinline__ uint32_t win8(uint4 v, const Clock& c) {
+  return pack8(win2(v.x, c), win2(v.y, c), win2(v.z, c), win2(v.w, c));
+}
+// Recorders whose bit is set in t (bit i = recorder i of the 8) take the stamp tm2.
+__device__ __forceinline__ uint32_t set2(uint32_t w, uint32_t t2, uint32_t tm2) {
+  const uint32_t m = ((t2 & 1u) * 0xFFFFu) | ((t2 >> 1) * 0xFFFF0000u);
+  return (w & ~m) | (tm2 & m);
+}
+__device__ __forceinline__ uint4 set8(uint4 v, uint32_t t, uint32_t tm2) {
+  return make_uint4(set2(v.x, t & 3u, tm2), set2(v.y, (t >> 2) & 3u, tm2), set2(v.z, (t >> 4) & 3u, tm2),
+                    set2(v.w, t >> 6, tm2));
+}
+// kNever (0xFFFF) in each recorder whose distance reaches 65535 at the advance, 0 elsewhere.
+__device__ __forceinline__ uint4 expire8(uint4 v, const Clock& c) {
+  return make_uint4(__vcmpeq2(v.x, c.xe2), __vcmpeq2(v.y, c.xe2), __vcmpeq2(v.z, c.xe2), __vcmpeq2(v.w, c.xe2));
+}
+// Clocks of a launch: one per sketch, read from device memory (captured work stays valid as the
+// sketches advance).
+__device__ __forceinline__ uint32_t read_tm(const uint32_t* tm) { return tm ? *tm : 0u; }
+
 // ---- scan (ssd_scan.cu) ----
 constexpr int kMaxBatch = SSD_MAX_ROUTERS;
 struct ScanJob {
@@ -108,6 +195,7 @@ struct ScanBatch {
   int n;
   uint64_t prefix[kMaxBatch + 1];  // prefix sums of nvec
   uint16_t* dr[kMaxBatch];
+  const uint32_t* tm[kMaxBatch];        // each job's sketch clock (the stamp its scan stores)
   const uint4* vec[kMaxBatch];
   const uint32_t* edge[2 * kMaxBatch];  // head, tail per router (nullptr when absent)
   uint32_t view[kMaxBatch];             // each job's sketch view (view_pair)
@@ -137,7 +225,10 @@ cudaError_t launch_scan(const Dims& d, const uint32_t* tables, const ScanBatch& 
 struct StreamArgs {
   int n;                               // routers
   uint16_t* routers[kMaxBatch];
+  const uint32_t* tm[kMaxBatch];       // each router's clock; nullptr: the recorders hold distances
+                                       // (read-only passes of the allocation-free regain)
   uint16_t* global;                    // merged output, or nullptr
+  uint32_t* global_tm;                 // its clock, set to router 0's (the merged state of this slot)
   uint64_t se0;                        // first estimator of the pass
   uint64_t se_count;                   // estimators in the pass; 0 = all r * 2^q from se0 = 0
   uint8_t* touch;                      // touch bits of the pass's estimators per router, or nullptr:
@@ -145,7 +236,8 @@ struct StreamArgs {
                                        // (j * se_count + e) * eta + x; applied (recorder := 0) and cleared
 };
 // mode bits
-constexpr int kAdvance = 1;   // routers += 1 (saturating) after reading
+constexpr int kAdvance = 1;   // routers advanced (expired recorders stored as kNever; the clocks are
+                              // moved on by launch_tick after every launch that reads them)
 constexpr int kHot = 2;       // count R_k of the merged value and pool the hot estimators
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
                           const Tuning& tn, cudaStream_t st);
@@ -277,7 +369,9 @@ cudaError_t launch_lists(const Dims& d, const uint32_t* tables, const ScanBatch&
 // next chunk [nx_se0, nx_se0 + nx_count) from the slot's pairs.
 struct ChunkArgs {
   uint16_t* router;
+  const uint32_t* tm;        // the router's clock
   uint16_t* global;          // merged output, or nullptr
+  uint32_t* global_tm;       // its clock (set to the router's)
   uint64_t se0, count;
   uint8_t* touch;            // this chunk's touch bits (cleared as they are applied)
   uint32_t* next;            // next chunk's touch bits, or nullptr
@@ -293,15 +387,27 @@ struct ChunkArgs {
 cudaError_t launch_chunk(const Dims& d, const Scratch& s, const ChunkArgs& a, int sms, const Tuning& tn,
                          cudaStream_t st);
 
+// ---- sketch clocks and conversions (ssd_stream.cu) ----
+// Every clock of tms moves on by one slot (tm_next), after the launches of an advance.
+struct TickArgs {
+  int n;
+  uint32_t* tm[kMaxBatch];
+};
+cudaError_t launch_tick(const TickArgs& a, cudaStream_t st);
+// dst[i] = flip(src[i]) for i < count at clock *tm_in (or tm_val when tm_in is nullptr): stamps to
+// distances (export) or distances to stamps (import). With tm_out the clock is also stored there.
+cudaError_t launch_flip(const uint16_t* src, uint16_t* dst, uint64_t count, const uint32_t* tm_in, uint32_t tm_val,
+                        uint32_t* tm_out, int sms, cudaStream_t st);
+
 // ---- reduction of a merge spread over GPUs (ssd_shard.cu) ----
 // out[x] = min over j < n of in[j][x] for x < count (all 16-byte aligned; out may be an input).
 cudaError_t launch_min_ranges(uint16_t* out, const uint16_t* const* in, int n, uint64_t count, int sms,
                               cudaStream_t st);
 
 // ---- diagnostics (ssd_diag.cu) ----
-// rk_sum[i] += sum over row i's estimators of R_k (recorders below k); eta >= 8.
-cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, unsigned long long* rk_sum, int sms,
-                             cudaStream_t st);
+// rk_sum[i] += sum over row i's estimators of R_k (recorders below k, stamps at clock *tm); eta >= 8.
+cudaError_t launch_occupancy(const Dims& d, const uint16_t* dr, const uint32_t* tm, unsigned long long* rk_sum,
+                             int sms, cudaStream_t st);
 
 // ---- regain (ssd_regain.cu) ----
 // Candidate levels, final test and the list; reads the pools filled by a kHot pass.

@@ -2,7 +2,8 @@
 //
 // Each thread takes 16-byte vectors of the pair stream (two packets per
 // vector), hashes both addresses with the simple-tabulation tables held in
-// shared memory, and sets the r recorders RSEA[i, RHFG[i](cip)][H1(oip)] to 0.
+// shared memory, and sets the r recorders RSEA[i, RHFG[i](cip)][H1(oip)] to 0,
+// which for the library's stamp recorders is a store of the sketch's clock.
 // Setting a recorder to 0 is idempotent and order-free (Sec. 4.1), so the
 // stores need no atomics and no ordering between threads.
 #include "ssd_internal.cuh"
@@ -12,27 +13,28 @@ namespace {
 
 // Algorithm 2 for one pair: DRidx = H1(oip); RHFG[0](cip) from the second table
 // set; RHFG[i](cip) = ((cip >> (i-1)*delta) ^ RHFG[0](cip)) mod 2^q for i >= 1.
-__device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint32_t cip, uint32_t oip,
+// The recorders take distance 0: the stamp `now` (the sketch's clock).
+__device__ __forceinline__ void scan_pair(uint16_t* __restrict__ dr, uint16_t now, uint32_t cip, uint32_t oip,
                                           const uint32_t* sT, const Dims& d) {
   const uint32_t j = tab_hash(sT, oip) & (d.eta - 1u);
   const uint32_t c0 = tab_hash(sT + 1024, cip) & d.col_mask;
-  if (in_bounds(d, j < d.eta && c0 < (1u << d.q))) dr[((uint64_t)c0 << d.log2_eta) | j] = 0;
+  if (in_bounds(d, j < d.eta && c0 < (1u << d.q))) dr[((uint64_t)c0 << d.log2_eta) | j] = now;
 #pragma unroll
   for (uint32_t i = 1; i < SSD_MAX_R; ++i) {
     if (i < d.r) {
       const uint32_t sh = (i - 1u) * d.delta + d.sh0;
       const uint32_t w = sh < 32u ? (cip >> sh) : 0u;
       const uint32_t col = (w ^ c0) & d.col_mask;
-      if (in_bounds(d, col < (1u << d.q))) dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = 0;
+      if (in_bounds(d, col < (1u << d.q))) dr[((((uint64_t)i << d.q) | col) << d.log2_eta) | j] = now;
     }
   }
 }
 
 // scan_pair on the stored pair (x, y) through a job's view (side and group).
-__device__ __forceinline__ void scan_view(uint16_t* __restrict__ dr, uint32_t view, uint32_t x, uint32_t y,
-                                          const uint32_t* sT, const Dims& d) {
+__device__ __forceinline__ void scan_view(uint16_t* __restrict__ dr, uint16_t now, uint32_t view, uint32_t x,
+                                          uint32_t y, const uint32_t* sT, const Dims& d) {
   uint32_t cip, oip;
-  if (view_pair(view, x, y, cip, oip)) scan_pair(dr, cip, oip, sT, d);
+  if (view_pair(view, x, y, cip, oip)) scan_pair(dr, now, cip, oip, sT, d);
 }
 
 // touch_pair on the stored pair (x, y) through a job's view; every lane makes the
@@ -60,14 +62,17 @@ template <int U>
 __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* __restrict__ tables,
                                                  const __grid_constant__ ScanBatch b) {
   __shared__ uint32_t sT[2048];
+  __shared__ uint16_t sNow[kMaxBatch];   // each job's stamp: its sketch's clock
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = tables[i];
+  if (threadIdx.x < b.n) sNow[threadIdx.x] = (uint16_t)read_tm(b.tm[threadIdx.x]);
   __syncthreads();
 
   // packets outside the 16-byte aligned bodies: a head when a buffer starts at
   // 8 mod 16, a tail when the body leaves one packet over
   if (blockIdx.x == 0 && threadIdx.x < 2 * b.n) {
     const uint32_t* e = b.edge[threadIdx.x];
-    if (e) scan_view(b.dr[threadIdx.x >> 1], b.view[threadIdx.x >> 1], e[0], e[1], sT, d);
+    const int j = threadIdx.x >> 1;
+    if (e) scan_view(b.dr[j], sNow[j], b.view[j], e[0], e[1], sT, d);
   }
 
   const uint64_t total = b.prefix[b.n];
@@ -77,45 +82,45 @@ __global__ void __launch_bounds__(kBlock) k_scan(const Dims d, const uint32_t* _
     const uint4* __restrict__ vec = b.vec[0];
     uint16_t* __restrict__ dr = b.dr[0];
     const uint32_t view = b.view[0];
+    const uint16_t now = sNow[0];
     for (; v + (U - 1) * stride < total; v += U * stride) {
       uint4 w[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) w[u] = __ldcs(vec + v + u * stride);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        scan_view(dr, view, w[u].x, w[u].y, sT, d);
-        scan_view(dr, view, w[u].z, w[u].w, sT, d);
+        scan_view(dr, now, view, w[u].x, w[u].y, sT, d);
+        scan_view(dr, now, view, w[u].z, w[u].w, sT, d);
       }
     }
     for (; v < total; v += stride) {
       const uint4 w = __ldcs(vec + v);
-      scan_view(dr, view, w.x, w.y, sT, d);
-      scan_view(dr, view, w.z, w.w, sT, d);
+      scan_view(dr, now, view, w.x, w.y, sT, d);
+      scan_view(dr, now, view, w.z, w.w, sT, d);
     }
   } else {
     for (; v + (U - 1) * stride < total; v += U * stride) {
       uint4 w[U];
-      uint16_t* dr[U];
-      uint32_t vw[U];
+      int jj[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint64_t vv = v + u * stride;
         const int j = find_router(b, vv);
         w[u] = __ldcs(b.vec[j] + (vv - b.prefix[j]));
-        dr[u] = b.dr[j];
-        vw[u] = b.view[j];
+        jj[u] = j;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        scan_view(dr[u], vw[u], w[u].x, w[u].y, sT, d);
-        scan_view(dr[u], vw[u], w[u].z, w[u].w, sT, d);
+        const int j = jj[u];
+        scan_view(b.dr[j], sNow[j], b.view[j], w[u].x, w[u].y, sT, d);
+        scan_view(b.dr[j], sNow[j], b.view[j], w[u].z, w[u].w, sT, d);
       }
     }
     for (; v < total; v += stride) {
       const int j = find_router(b, v);
       const uint4 w = __ldcs(b.vec[j] + (v - b.prefix[j]));
-      scan_view(b.dr[j], b.view[j], w.x, w.y, sT, d);
-      scan_view(b.dr[j], b.view[j], w.z, w.w, sT, d);
+      scan_view(b.dr[j], sNow[j], b.view[j], w.x, w.y, sT, d);
+      scan_view(b.dr[j], sNow[j], b.view[j], w.z, w.w, sT, d);
     }
   }
 }

@@ -3,14 +3,16 @@
 //
 // One kernel serves every combination: for each recorder position it reads the
 // n routers' values (16 bytes = 8 recorders per lane), optionally sets the
-// recorders whose touch bit is set to 0 first (Algorithm 2 deferred from the
-// scan of the fused slot; the bit is cleared), takes the elementwise minimum
-// over routers (the merge), optionally writes that to the global RSEA,
-// optionally counts the merged recorders below k per estimator and pools the hot
-// ones with their "recorder < k" bitmap, and optionally writes every router's
-// value back advanced by one with saturation at 65535. Recorders are read and
-// written once per pass, in 512-byte coalesced warp accesses with streaming
-// cache hints; the touch bits stay in L2.
+// recorders whose touch bit is set to distance 0 first (Algorithm 2 deferred
+// from the scan of the fused slot; the bit is cleared), takes the elementwise
+// minimum distance over routers (the merge), optionally writes that to the
+// global RSEA, optionally counts the merged recorders below k per estimator and
+// pools the hot ones with their "recorder < k" bitmap, and optionally advances
+// every router by one slot. The recorders are stamps (ssd_internal.cuh): the
+// advance itself is the clock's tick, so a router's vector is written back only
+// when one of its recorders was set by a touch or reaches distance 65535.
+// Recorders are read once per pass, in 512-byte coalesced warp accesses with
+// streaming cache hints; the touch bits stay in L2.
 #include "ssd_internal.cuh"
 
 namespace ssd {
@@ -18,14 +20,12 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// 8 recorders (two per 32-bit word) advanced by one, saturating at 65535: no
-// carry can cross a half because each half is at most 65534 before the add.
-__device__ __forceinline__ uint32_t inc2(uint32_t w) { return __vminu2(w, 0xFFFEFFFEu) + 0x00010001u; }
-__device__ __forceinline__ uint4 inc8(uint4 v) { return make_uint4(inc2(v.x), inc2(v.y), inc2(v.z), inc2(v.w)); }
 __device__ __forceinline__ uint4 min8(uint4 a, uint4 b) {
   return make_uint4(__vminu2(a.x, b.x), __vminu2(a.y, b.y), __vminu2(a.z, b.z), __vminu2(a.w, b.w));
 }
-// bit i of the result = (recorder i < k) for the 8 recorders of v
+__device__ __forceinline__ uint4 or8(uint4 a, uint4 b) { return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w); }
+__device__ __forceinline__ bool any8(uint4 a) { return (a.x | a.y | a.z | a.w) != 0u; }
+// bit i of the result = (distance i < k) for the 8 distances of v
 __device__ __forceinline__ uint32_t lt2(uint32_t w, uint32_t kk) {
   const uint32_t k = kk & 0xFFFFu;
   return (uint32_t)((w & 0xFFFFu) < k) | ((uint32_t)((w >> 16) < k) << 1);
@@ -33,12 +33,18 @@ __device__ __forceinline__ uint32_t lt2(uint32_t w, uint32_t kk) {
 __device__ __forceinline__ uint32_t lt8(uint4 v, uint32_t kk) {
   return lt2(v.x, kk) | (lt2(v.y, kk) << 2) | (lt2(v.z, kk) << 4) | (lt2(v.w, kk) << 6);
 }
-// recorders whose bit is set in t (bit i = recorder i of the 8) become 0
-__device__ __forceinline__ uint32_t zero2(uint32_t w, uint32_t t2) {
-  return w & ~(((t2 & 1u) * 0xFFFFu) | ((t2 >> 1) * 0xFFFF0000u));
-}
-__device__ __forceinline__ uint4 apply8(uint4 v, uint32_t t) {
-  return make_uint4(zero2(v.x, t & 3u), zero2(v.y, (t >> 2) & 3u), zero2(v.z, (t >> 4) & 3u), zero2(v.w, t >> 6));
+
+// The clock of router j of a pass: its tm and expiry stamp in both halves (stamp recorders), or
+// tm2 = 0 and `stamps` false when the pass reads distances.
+struct RouterClock {
+  uint32_t tm2, xe2;
+};
+__device__ __forceinline__ RouterClock router_clock(const uint32_t* tm) {
+  RouterClock rc;
+  const uint32_t t = read_tm(tm), xe = tm_next(t);
+  rc.tm2 = t | (t << 16);
+  rc.xe2 = xe | (xe << 16);
+  return rc;
 }
 
 // Pool a hot estimator: reserve a slot in its row's pool and return it
@@ -75,29 +81,40 @@ __device__ __forceinline__ void load_group(const uint4* r0, uint64_t base, const
   }
 }
 
-// The loaded group: touch bits applied (and cleared), merged value written to
-// g, "< k" bits to `my` (shared) and counted, recorders advanced. Returns the
-// lane's count of recorders below k in the group.
+// The loaded group of one router's stamps: touch bits applied (those recorders take the stamp tm,
+// distance 0; the bits are cleared), the state written to g, the window bits ("distance < k") to
+// `my` (shared) and counted, and the vectors that changed - a recorder set by a touch or, with
+// ADV, one whose distance reaches 65535 at this advance (it becomes kNever) - written back.
+// Returns the lane's count of recorders inside the window.
 template <bool ADV, bool HOT, bool TOUCH>
 __device__ __forceinline__ uint32_t proc_group(uint4* r0, uint4* g, uint64_t base, uint8_t* tb, uint8_t* my,
-                                               uint32_t it0, uint32_t m, int lane, uint32_t kk, uint4 (&v)[8],
+                                               uint32_t it0, uint32_t m, int lane, const Clock& c, uint4 (&v)[8],
                                                const uint32_t (&t)[8]) {
   uint32_t cnt = 0;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (u < (int)m) {
       const uint64_t at = base + (it0 + u) * 32 + lane;
+      bool dirty = false;
       if (TOUCH && t[u]) {
-        v[u] = apply8(v[u], t[u]);
+        v[u] = set8(v[u], t[u], c.tm2);
         tb[(it0 + u) * 32] = 0;
+        dirty = true;
       }
       if (g) __stcs(g + at, v[u]);
       if (HOT) {
-        const uint32_t bits = lt8(v[u], kk);
+        const uint32_t bits = win8(v[u], c);
         cnt += __popc(bits);
         my[(it0 + u) * 32 + lane] = (uint8_t)bits;
       }
-      if (ADV) __stcs(r0 + at, inc8(v[u]));
+      if (ADV) {
+        const uint4 e = expire8(v[u], c);
+        if (any8(e)) {
+          v[u] = or8(v[u], e);
+          dirty = true;
+        }
+      }
+      if (dirty) __stcs(r0 + at, v[u]);
     }
   }
   return cnt;
@@ -108,16 +125,15 @@ __device__ __forceinline__ uint32_t proc_group(uint4* r0, uint4* g, uint64_t bas
 // touch bits. Returns the lane's count of recorders below k.
 template <bool ADV, bool HOT, bool TOUCH>
 __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint4* g, uint64_t base, uint8_t* tb,
-                                                  uint8_t* my, int lane) {
+                                                  uint8_t* my, int lane, const Clock& c) {
   const uint32_t iters = d.eta >> 8;
-  const uint32_t kk = d.k | (d.k << 16);
   uint32_t cnt = 0;
   for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
     const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
     uint4 v[8];
     uint32_t t[8];
     load_group<TOUCH>(r0, base, tb, it0, m, lane, v, t);
-    cnt += proc_group<ADV, HOT, TOUCH>(r0, g, base, tb, my, it0, m, lane, kk, v, t);
+    cnt += proc_group<ADV, HOT, TOUCH>(r0, g, base, tb, my, it0, m, lane, c, v, t);
   }
   return cnt;
 }
@@ -147,11 +163,14 @@ __device__ __forceinline__ void pool_if_hot(const Dims& d, const Scratch& s, uin
 }
 
 // eta >= 256: one warp per estimator, iters = eta/256 steps of 32 lanes x 8 recorders.
-// G (several routers): routers loaded per group before any of them is stored.
+// G (several routers): routers loaded per group before any of them is stored. One router works on
+// its stamps directly (window test, expiry); several routers are merged as distances (each
+// router's stamps through its own clock), and the global RSEA takes router 0's clock.
 template <bool ONE, bool ADV, bool HOT, bool TOUCH, int G>
 __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) uint8_t smask[];
+  __shared__ RouterClock sck[ONE ? 1 : kMaxBatch];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* my = smask + (size_t)wid * (d.eta >> 3);
   const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
@@ -161,17 +180,25 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
   const uint64_t wstride = (uint64_t)gridDim.x * (kBlock / 32);
   const uint64_t tstride = count * (d.eta >> 3);  // touch bytes per router
   uint4* const g = reinterpret_cast<uint4*>(a.global);
+  const bool stamps = a.tm[0] != nullptr;
+  const uint32_t tm0 = read_tm(a.tm[0]);
+  const Clock c = stamps ? make_clock(tm0, d.k) : distance_clock(d.k);
+  if (a.global_tm && blockIdx.x == 0 && threadIdx.x == 0) *a.global_tm = tm0;
+  if (!ONE) {
+    for (int j = threadIdx.x; j < a.n; j += blockDim.x) sck[j] = router_clock(a.tm[j]);
+    __syncthreads();
+  }
 
   for (uint64_t se = a.se0 + (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < se_end; se += wstride) {
     const uint64_t base = (se << d.log2_eta) >> 3;  // in 8-recorder units
     uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane : nullptr;
     uint32_t cnt = 0;
     if (ONE) {
-      cnt = one_router_se<ADV, HOT, TOUCH>(d, reinterpret_cast<uint4*>(a.routers[0]), g, base, tb, my, lane);
+      cnt = one_router_se<ADV, HOT, TOUCH>(d, reinterpret_cast<uint4*>(a.routers[0]), g, base, tb, my, lane, c);
     } else {
       for (uint32_t it = 0; it < iters; ++it) {
         const uint64_t at = base + it * 32 + lane;
-        uint4 mv = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        uint4 mv = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);   // distances
         // routers in groups of G: the group's loads are issued before any of its stores
         for (int n0 = 0; n0 < a.n; n0 += G) {
           const int m = a.n - n0 < G ? a.n - n0 : G;
@@ -187,16 +214,27 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
 #pragma unroll
           for (int u = 0; u < G; ++u) {
             if (u < m) {
+              const RouterClock rc = sck[n0 + u];
+              bool dirty = false;
               if (TOUCH && t[u]) {
-                v[u] = apply8(v[u], t[u]);
+                v[u] = set8(v[u], t[u], rc.tm2);
                 tb[(uint64_t)(n0 + u) * tstride + it * 32] = 0;
+                dirty = true;
               }
-              mv = min8(mv, v[u]);
-              if (ADV) __stcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at, inc8(v[u]));
+              mv = min8(mv, stamps ? flip8(v[u], rc.tm2) : v[u]);
+              if (ADV) {
+                const uint4 e = make_uint4(__vcmpeq2(v[u].x, rc.xe2), __vcmpeq2(v[u].y, rc.xe2),
+                                           __vcmpeq2(v[u].z, rc.xe2), __vcmpeq2(v[u].w, rc.xe2));
+                if (any8(e)) {
+                  v[u] = or8(v[u], e);
+                  dirty = true;
+                }
+              }
+              if (dirty) __stcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at, v[u]);
             }
           }
         }
-        if (g) __stcs(g + at, mv);
+        if (g) __stcs(g + at, stamps ? flip8(mv, c.tm2) : mv);
         if (HOT) {
           const uint32_t bits = lt8(mv, kk);
           cnt += __popc(bits);
@@ -208,10 +246,12 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
   }
 }
 
-// 32 <= eta <= 128: L = eta/8 lanes per estimator, 32/L estimators per warp step.
+// 32 <= eta <= 128: L = eta/8 lanes per estimator, 32/L estimators per warp step. Routers are
+// merged as distances (each router's stamps through its own clock).
 template <bool ONE, bool ADV, bool HOT, bool TOUCH>
 __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scratch s,
                                                          const __grid_constant__ StreamArgs a) {
+  __shared__ RouterClock sck[ONE ? 1 : kMaxBatch];
   const int lane = threadIdx.x & 31;
   const uint32_t L = d.eta >> 3;
   const uint32_t per_warp = 32u / L;
@@ -223,25 +263,46 @@ __global__ void __launch_bounds__(kBlock) k_stream_small(const Dims d, const Scr
   const uint64_t tstride = count * (d.eta >> 3);
   uint4* const g = reinterpret_cast<uint4*>(a.global);
   uint8_t* const bm_bytes = reinterpret_cast<uint8_t*>(s.pool_bm);
+  const bool stamps = a.tm[0] != nullptr;
+  if (a.global_tm && blockIdx.x == 0 && threadIdx.x == 0) *a.global_tm = read_tm(a.tm[0]);
+  for (int j = threadIdx.x; j < (ONE ? 1 : a.n); j += blockDim.x) sck[j] = router_clock(a.tm[j]);
+  __syncthreads();
+
+  // router n's vector at `at`: touch applied, written back when it changed; returns its distances
+  auto one = [&](int n, uint64_t at, uint8_t* t8) {
+    const RouterClock rc = sck[n];
+    uint4* rp = reinterpret_cast<uint4*>(a.routers[n]);
+    uint4 v = __ldcs(rp + at);
+    bool dirty = false;
+    if (TOUCH) {
+      const uint32_t t = take_touch(t8);
+      if (t) {
+        v = set8(v, t, rc.tm2);
+        dirty = true;
+      }
+    }
+    const uint4 dist = stamps ? flip8(v, rc.tm2) : v;
+    if (ADV) {
+      const uint4 e = make_uint4(__vcmpeq2(v.x, rc.xe2), __vcmpeq2(v.y, rc.xe2), __vcmpeq2(v.z, rc.xe2),
+                                 __vcmpeq2(v.w, rc.xe2));
+      if (any8(e)) {
+        v = or8(v, e);
+        dirty = true;
+      }
+    }
+    if (dirty) __stcs(rp + at, v);
+    return dist;
+  };
 
   for (uint64_t uu = (uint64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); uu < n_units; uu += wstride) {
     const uint64_t u = u0 + uu;
     const uint64_t at = u * 32 + lane;
     uint8_t* tb = TOUCH ? a.touch + uu * 32 + lane : nullptr;  // byte of these 8 recorders, router 0
-    uint4* rp = reinterpret_cast<uint4*>(a.routers[0]);
-    uint4 mv = __ldcs(rp + at);
-    if (TOUCH) mv = apply8(mv, take_touch(tb));
-    if (ADV) __stcs(rp + at, inc8(mv));
+    uint4 mv = one(0, at, tb);
     if (!ONE) {
-      for (int n = 1; n < a.n; ++n) {
-        rp = reinterpret_cast<uint4*>(a.routers[n]);
-        uint4 v = __ldcs(rp + at);
-        if (TOUCH) v = apply8(v, take_touch(tb + n * tstride));
-        mv = min8(mv, v);
-        if (ADV) __stcs(rp + at, inc8(v));
-      }
+      for (int n = 1; n < a.n; ++n) mv = min8(mv, one(n, at, TOUCH ? tb + n * tstride : nullptr));
     }
-    if (g) __stcs(g + at, mv);
+    if (g) __stcs(g + at, stamps ? flip8(mv, sck[0].tm2) : mv);
     if (HOT) {
       const uint32_t bits = lt8(mv, kk);
       uint32_t cnt = __popc(bits);
@@ -272,7 +333,7 @@ constexpr int kSrcList = 3;     // the next chunk's touch list: bit indices writ
 
 // One chunk of the fused slot of one router (eta >= 256): each warp streams
 // estimators of the chunk with their touch bits applied, counts and pools hot
-// ones and advances; unless SRC is kSrcNone, between estimators each lane also
+// ones and writes back the vectors that changed (touched or expired); unless SRC is kSrcNone, between estimators each lane also
 // sets a share of the next chunk's touch bits (L2 atomics that fill the gaps of
 // the memory-bound stream), from the next chunk's touch list or by hashing a
 // share of the slot's pairs. The pairs or list entries are walked warp by warp
@@ -311,6 +372,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
     load_group<false>(reinterpret_cast<const uint4*>(a.router), ((a.se0 + e_first) << d.log2_eta) >> 3, nullptr, 0,
                       m0, lane, v, t);
   asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous grid has completed
+  // the router's clock (moved on only after the slot's last launch)
+  const uint32_t tm = *a.tm;
+  const Clock c = make_clock(tm, d.k);
+  if (a.global_tm && blockIdx.x == 0 && threadIdx.x == 0) *a.global_tm = tm;
   // entries of the next chunk's touch list (written by the list launch before chunk 0)
   const uint64_t n_items = LIST ? (uint64_t)*a.list_fill : a.nvec;
   const uint32_t nr0 = NEXT ? (uint32_t)(a.nx_se0 >> d.q) : 0u;
@@ -330,7 +395,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
       touch_pair<CM>(a.next, 0, c1, o1, live && in1, sT, d, nr0, nr1, a.nx_se0, a.nx_count);
     }
   };
-  const uint32_t kk = d.k | (d.k << 16);
   // after an estimator's pass: its share of the next chunk's touches, then its pooling
   auto finish = [&](uint64_t e, uint64_t se, uint32_t cnt, uint4 w0) {
     const uint64_t vb0 = e * 32;
@@ -375,11 +439,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (u < (int)m0) t[u] = tb[u * 32];
-    uint32_t cnt = proc_group<true, true, true>(r0, g, base, tb, my, 0, m0, lane, kk, v, t);
+    uint32_t cnt = proc_group<true, true, true>(r0, g, base, tb, my, 0, m0, lane, c, v, t);
     for (uint32_t it0 = 8; it0 < iters; it0 += 8) {
       const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
       load_group<true>(r0, base, tb, it0, m, lane, v, t);
-      cnt += proc_group<true, true, true>(r0, g, base, tb, my, it0, m, lane, kk, v, t);
+      cnt += proc_group<true, true, true>(r0, g, base, tb, my, it0, m, lane, c, v, t);
     }
     finish(e, se, cnt, w0);
     e += wstride;
@@ -388,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
     const uint64_t se = a.se0 + e;
     const uint4 w0 = first_pair(e);
     const uint32_t cnt =
-        one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, a.touch + e * tstep + lane, my, lane);
+        one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, a.touch + e * tstep + lane, my, lane, c);
     finish(e, se, cnt, w0);
   }
 }
@@ -430,7 +494,40 @@ cudaError_t launch_variant(const Dims& d, const Scratch& s, const StreamArgs& a,
   return cudaGetLastError();
 }
 
+// The clocks of an advance move on by one slot.
+__global__ void k_tick(const __grid_constant__ TickArgs a) {
+  if ((int)threadIdx.x < a.n) *a.tm[threadIdx.x] = tm_next(*a.tm[threadIdx.x]);
+}
+
+// dst = flip(src) at one clock; the clock is also stored at tm_out (by one thread).
+__global__ void __launch_bounds__(kBlock) k_flip(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst,
+                                                 uint64_t count, const uint32_t* tm_in, uint32_t tm_val,
+                                                 uint32_t* tm_out) {
+  const uint32_t tm = tm_in ? *tm_in : tm_val;
+  const uint32_t tm2 = tm | (tm << 16);
+  if (tm_out && blockIdx.x == 0 && threadIdx.x == 0) *tm_out = tm;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    dst[i] = (uint16_t)flip2(src[i], tm2);
+}
+
 }  // namespace
+
+cudaError_t launch_tick(const TickArgs& a, cudaStream_t st) {
+  if (a.n < 1 || a.n > kMaxBatch) return cudaErrorInvalidValue;
+  k_tick<<<1, kMaxBatch, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip(const uint16_t* src, uint16_t* dst, uint64_t count, const uint32_t* tm_in, uint32_t tm_val,
+                        uint32_t* tm_out, int sms, cudaStream_t st) {
+  if (!count && !tm_out) return cudaSuccess;
+  uint64_t grid = (count + kBlock - 1) / kBlock;
+  if (grid > (uint64_t)sms * 8) grid = (uint64_t)sms * 8;
+  if (grid < 1) grid = 1;
+  k_flip<<<(unsigned)grid, kBlock, 0, st>>>(src, dst, count, tm_in, tm_val, tm_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stream(const Dims& d, const Scratch& s, const StreamArgs& a, int mode, int sms,
                           const Tuning& tn, cudaStream_t st) {

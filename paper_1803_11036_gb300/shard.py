@@ -5,13 +5,17 @@ which merges them with UnionSE (Sec. 4); it leaves the transport open. Here each
 holds the RSEAs of some routers, and the end of a slot runs in four steps:
 
 1. local merge: the rank's routers are merged on its GPU (ssd_merge, the minimum of the union
-   reading) into one RSEA;
+   reading) into one RSEA, read out as distance recorders (ssd_sketch_export to device memory);
 2. reduce-scatter by recorder range: that RSEA is cut into `world` ranges of whole estimators;
    range j goes to rank j (one all_to_all of bytes), which folds the `world` slices it then holds
    with the elementwise minimum (ssd_min_merge) into its range of the global RSEA;
-3. gather: the root rank receives every range straight into its global sketch and regains the
-   sliding super points (ssd_regain); the other ranks send theirs;
+3. gather: the root rank receives every range into one distance array, loads it into its global
+   sketch (ssd_sketch_import from device memory) and regains the sliding super points
+   (ssd_regain); the other ranks send theirs;
 4. every rank advances its routers (ssd_advance).
+
+The exchange carries distances, not the library's stored stamps, so it does not depend on the
+ranks' sketch clocks.
 
 Per slot every rank sends and receives (world-1)/world of one RSEA in step 2, and the root
 receives (world-1)/world of one more in step 3, however many routers a rank holds. Collective
@@ -104,20 +108,28 @@ class ShardedDetector:
         self.glob = ctx.sketch().set_view(*view) if self.rank == root else None
         p = ctx.params
         self.ranges = estimator_ranges(p.r << p.q, 1 << p.log2_eta, self.world)
+        self._local_dist = None      # the local merge as distances (step 1)
+        self._global_dist = None     # the gathered global RSEA as distances (root, step 3)
 
     def _fold(self, out, slices):
         self.ctx.min_merge(out, slices)
 
     def close_slot(self, cap: int = 1 << 16):
+        import torch
         ctx = self.ctx
         ctx.merge(self.routers, self.local)                               # step 1
-        shard = reduce_scatter_min(self.local.device_view(), self.ranges, self.rank, self._fold,
+        self._local_dist = self.local.export_device(self._local_dist)
+        shard = reduce_scatter_min(self._local_dist, self.ranges, self.rank, self._fold,
                                    self.group)                            # step 2
-        dest = self.glob.device_view() if self.glob is not None else None
+        dest = None
+        if self.glob is not None:
+            if self._global_dist is None:
+                self._global_dist = torch.empty_like(self._local_dist)
+            dest = self._global_dist
         gather_ranges(shard, self.ranges, self.rank, self.root, dest, self.group)   # step 3
         result = None
         if self.glob is not None:
-            self.glob.slot = self.routers[0].slot
+            self.glob.load_device(self._global_dist, self.routers[0].slot)
             result = ctx.regain(self.glob, cap=cap)
         ctx.advance(self.routers)                                         # step 4
         return result

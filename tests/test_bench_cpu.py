@@ -55,17 +55,19 @@ def test_gbps_conventions():
 
 def test_step_rooflines_split():
     """The per-step block: the scan's marginal cost is the pass with the scan minus the close-only
-    pass; each fraction is algorithmic bytes / time / peak."""
+    pass; each fraction is algorithmic bytes / time / peak, where the close-only pass reads every
+    recorder once (rec_bytes) and the slot's pass adds the scan's 18 B per packet."""
     s = bench.step_rooflines(pk=6.25e6, scan_ms=1.0, scan_pk=6.25e6, slot_pass=[1.9, 2.1], slot_tail=[0.14],
-                             close_pass=[1.7, 1.7], close_tail=[0.13], pass_bytes=10.0e9, r=5, peak=6000.0)
+                             close_pass=[1.7, 1.7], close_tail=[0.13], rec_bytes=5.0e9, r=5, peak=6000.0)
     assert abs(s["scan_in_slot"]["ms_per_slice"] - 0.3) < 1e-9
     assert s["scan_standalone"]["algorithmic_bytes_per_packet"] == 18
     assert abs(s["scan_standalone"]["frac"] - 18 * 6.25e6 / 1e-3 / 1e9 / 6000.0) < 1e-4
     assert abs(s["scan_in_slot"]["frac"] - 18 * 6.25e6 / 0.3e-3 / 1e9 / 6000.0) < 1e-4
     assert s["scan_in_slot"]["target_met"] is False
-    assert abs(s["slot_pass"]["frac"] - 10.0e9 / 2.0e-3 / 1e9 / 6000.0) < 1e-4
-    assert abs(s["close_pass"]["frac"] - 10.0e9 / 1.7e-3 / 1e9 / 6000.0) < 1e-4
+    assert s["slot_pass"]["algorithmic_bytes"] == 5.0e9 + 18 * 6.25e6
+    assert abs(s["slot_pass"]["frac"] - (5.0e9 + 18 * 6.25e6) / 2.0e-3 / 1e9 / 6000.0) < 1e-4
+    assert abs(s["close_pass"]["frac"] - 5.0e9 / 1.7e-3 / 1e9 / 6000.0) < 1e-4
     assert s["regain_tail"]["ms_per_slice"] == 0.14
     fast = bench.step_rooflines(pk=6.25e6, scan_ms=1.0, scan_pk=6.25e6, slot_pass=[1.701], slot_tail=[0.1],
-                                close_pass=[1.7], close_tail=[0.1], pass_bytes=1e9, r=5, peak=6000.0)
+                                close_pass=[1.7], close_tail=[0.1], rec_bytes=1e9, r=5, peak=6000.0)
     assert fast["scan_in_slot"]["target_met"] is True

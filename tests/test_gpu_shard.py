@@ -84,7 +84,7 @@ def test_emulated_ranks_fold_to_the_merged_rsea(world):
             mine = [routers[j] for j in range(R) if j % world == rank]
             if mine:
                 ctx.merge(mine, locals_[rank])
-        views = [locals_[rank].device_view() for rank in range(world) if any(j % world == rank for j in range(R))]
+        views = [locals_[rank].export_device() for rank in range(world) if any(j % world == rank for j in range(R))]
         glob = torch.empty(p.r * p.C * p.eta, dtype=torch.int16, device="cuda")
         for f, c in ranges:
             ctx.min_merge(glob[f:f + c], [v[f:f + c] for v in views])
