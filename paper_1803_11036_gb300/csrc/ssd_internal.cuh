@@ -123,6 +123,8 @@ __device__ __forceinline__ uint4 flip8(uint4 v, uint32_t tm2) {
 struct Clock {
   uint32_t tm2;     // tm, both halves
   uint32_t lo2;     // oldest stamp in the window, both halves
+  uint32_t hi2;     // newest stamp of the window's range starting at lo (tm, or 65534 when the window
+                    // wraps; k - 1 for distances), both halves
   uint32_t klim2;   // length of the window's 16-bit range, both halves
   uint32_t xe2;     // the stamp whose distance reaches 65535 at the advance, both halves
   uint32_t wrap;    // kNever lies in the 16-bit range of the window
@@ -135,6 +137,7 @@ __host__ __device__ __forceinline__ Clock make_clock(uint32_t tm, uint32_t k) {
   const uint32_t xe = tm_next(tm);
   c.tm2 = tm | (tm << 16);
   c.lo2 = lo | (lo << 16);
+  c.hi2 = wrap ? 0xFFFEFFFEu : c.tm2;
   c.klim2 = klim | (klim << 16);
   c.xe2 = xe | (xe << 16);
   c.wrap = wrap ? 1u : 0u;
@@ -144,6 +147,7 @@ __host__ __device__ __forceinline__ Clock distance_clock(uint32_t k) {
   Clock c;
   c.tm2 = 0u;
   c.lo2 = 0u;
+  c.hi2 = (k - 1u) | ((k - 1u) << 16);
   c.klim2 = k | (k << 16);
   c.xe2 = 0xFFFFFFFFu;   // never matched by a stored value that is advanced (no advance on distances)
   c.wrap = 0u;
@@ -173,6 +177,50 @@ __device__ __forceinline__ uint32_t set2(uint32_t w, uint32_t t2, uint32_t tm2) 
 __device__ __forceinline__ uint4 set8(uint4 v, uint32_t t, uint32_t tm2) {
   return make_uint4(set2(v.x, t & 3u, tm2), set2(v.y, (t >> 2) & 3u, tm2), set2(v.z, (t >> 4) & 3u, tm2),
                     set2(v.w, t >> 6, tm2));
+}
+// The same tests with fewer instructions: a stamp lies inside a range [lo, hi] (lo <= hi) exactly
+// when clamping it into the range leaves it unchanged. The window is [lo, tm], or [lo, 65534] and
+// [0, tm] when it wraps (kNever lies in neither). min/max.u16x2 are single instructions on sm_90
+// and later, where the compares and subtractions of 16-bit halves above are not.
+__device__ __forceinline__ uint32_t umin2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t umax2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+// 1 in each half of x outside [lo, hi], 0 inside.
+__device__ __forceinline__ uint32_t out_range2(uint32_t x, uint32_t lo2, uint32_t hi2) {
+  return umin2(umax2(umin2(x, hi2), lo2) ^ x, 0x00010001u);
+}
+// 1 in each half of x outside the window, 0 inside (so a sum of these words counts the recorders
+// outside, per half, in 16-bit fields). c.wrap is the same for the whole grid.
+__device__ __forceinline__ uint32_t out2(uint32_t x, const Clock& c) {
+  uint32_t o = out_range2(x, c.lo2, c.hi2);
+  if (c.wrap) o &= out_range2(x, 0u, c.tm2);
+  return o;
+}
+// Whether any of the 8 recorders holds the stamp xe (a zero half in x ^ xe).
+__device__ __forceinline__ bool any_eq8(uint4 v, uint32_t xe2) {
+  const uint32_t m = umin2(umin2(v.x ^ xe2, v.y ^ xe2), umin2(v.z ^ xe2, v.w ^ xe2));
+  return umin2(m, 0x00010001u) != 0x00010001u;
+}
+// The 16-bit masks of the recorders named by a touch byte (bit i = recorder i of 8): entry t of
+// a 256-entry table, one entry per thread of a block of at least 256 threads.
+__device__ __forceinline__ uint4 touch_mask_entry(uint32_t t) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = (((t >> (2 * i)) & 1u) ? 0xFFFFu : 0u) | (((t >> (2 * i + 1)) & 1u) ? 0xFFFF0000u : 0u);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+// Recorders of v under the mask mk take the stamp tm2.
+__device__ __forceinline__ uint4 set_masked(uint4 v, uint4 mk, uint32_t tm2) {
+  return make_uint4((v.x & ~mk.x) | (tm2 & mk.x), (v.y & ~mk.y) | (tm2 & mk.y), (v.z & ~mk.z) | (tm2 & mk.z),
+                    (v.w & ~mk.w) | (tm2 & mk.w));
 }
 // kNever (0xFFFF) in each recorder whose distance reaches 65535 at the advance, 0 elsewhere.
 __device__ __forceinline__ uint4 expire8(uint4 v, const Clock& c) {

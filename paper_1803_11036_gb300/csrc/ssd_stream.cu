@@ -82,50 +82,64 @@ __device__ __forceinline__ void load_group(const uint4* r0, uint64_t base, const
 }
 
 // The loaded group of one router's stamps: touch bits applied (those recorders take the stamp tm,
-// distance 0; the bits are cleared), the state written to g, the window bits ("distance < k") to
-// `my` (shared) and counted, and the vectors that changed - a recorder set by a touch or, with
-// ADV, one whose distance reaches 65535 at this advance (it becomes kNever) - written back.
+// distance 0; the masks come from the table tmask, built by touch_mask_entry; the bits are
+// cleared), the state written to g, the recorders inside the window counted (out2), and the
+// vectors that changed - a recorder set by a touch or, with ADV, one whose distance reaches 65535
+// at this advance (it becomes kNever; any_eq8 tests the whole vector first) - written back. No
+// window bits are written: the caller builds them with group_bits only for a hot estimator.
 // Returns the lane's count of recorders inside the window.
 template <bool ADV, bool HOT, bool TOUCH>
-__device__ __forceinline__ uint32_t proc_group(uint4* r0, uint4* g, uint64_t base, uint8_t* tb, uint8_t* my,
-                                               uint32_t it0, uint32_t m, int lane, const Clock& c, uint4 (&v)[8],
-                                               const uint32_t (&t)[8]) {
-  uint32_t cnt = 0;
+__device__ __forceinline__ uint32_t fast_group(uint4* r0, uint4* g, uint64_t base, uint8_t* tb, uint32_t it0,
+                                               uint32_t m, int lane, const Clock& c, const uint4* tmask,
+                                               uint4 (&v)[8], const uint32_t (&t)[8]) {
+  uint32_t out = 0;   // recorders outside the window, per half, in two 16-bit fields
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (u < (int)m) {
       const uint64_t at = base + (it0 + u) * 32 + lane;
       bool dirty = false;
       if (TOUCH && t[u]) {
-        v[u] = set8(v[u], t[u], c.tm2);
+        v[u] = set_masked(v[u], tmask[t[u]], c.tm2);
         tb[(it0 + u) * 32] = 0;
         dirty = true;
       }
       if (g) __stcs(g + at, v[u]);
-      if (HOT) {
-        const uint32_t bits = win8(v[u], c);
-        cnt += __popc(bits);
-        my[(it0 + u) * 32 + lane] = (uint8_t)bits;
-      }
-      if (ADV) {
-        const uint4 e = expire8(v[u], c);
-        if (any8(e)) {
-          v[u] = or8(v[u], e);
-          dirty = true;
-        }
+      if (HOT) out += out2(v[u].x, c) + out2(v[u].y, c) + out2(v[u].z, c) + out2(v[u].w, c);
+      if (ADV && any_eq8(v[u], c.xe2)) {
+        v[u] = or8(v[u], expire8(v[u], c));
+        dirty = true;
       }
       if (dirty) __stcs(r0 + at, v[u]);
     }
   }
-  return cnt;
+  return 8u * m - (out & 0xFFFFu) - (out >> 16);
 }
 
-// One estimator of one router, all eta recorders (eta >= 256), in groups of 8
-// vectors: load_group then proc_group. tb: this lane's byte of the estimator's
-// touch bits. Returns the lane's count of recorders below k.
+// The window bits of a group fast_group has processed, to `my`, from the recorders read again one
+// vector at a time (the lane reads back the vectors it stored itself; a hot estimator is rare, so
+// nothing is kept live in registers for it). A recorder the advance expired holds kNever, outside the window, as its
+// stamp xe was.
+__device__ __forceinline__ void group_bits(const uint4* r0, uint64_t base, uint32_t it0, uint32_t m, uint8_t* my,
+                                           int lane, const Clock& c) {
+#pragma unroll 1
+  for (uint32_t u = 0; u < m; ++u)
+    my[(it0 + u) * 32 + lane] = (uint8_t)win8(__ldcg(r0 + base + (it0 + u) * 32 + lane), c);
+}
+
+// The window bits of every group of an estimator whose warp-wide count reaches the threshold.
+__device__ __forceinline__ void hot_bits(const Dims& d, const uint4* r0, uint64_t base, uint32_t cnt, uint8_t* my,
+                                         int lane, const Clock& c) {
+  if (__reduce_add_sync(kFull, cnt) < d.thr) return;   // warp-uniform
+  const uint32_t iters = d.eta >> 8;
+  for (uint32_t it0 = 0; it0 < iters; it0 += 8) group_bits(r0, base, it0, iters - it0 < 8u ? iters - it0 : 8u, my, lane, c);
+}
+
+// One estimator of one router, all eta recorders (eta >= 256), in groups of 8 vectors per lane:
+// load_group then fast_group, then the window bits only when the warp's count reaches the
+// threshold (pool_if_hot pools it). tb: this lane's byte of the estimator's touch bits.
 template <bool ADV, bool HOT, bool TOUCH>
 __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint4* g, uint64_t base, uint8_t* tb,
-                                                  uint8_t* my, int lane, const Clock& c) {
+                                                  uint8_t* my, int lane, const Clock& c, const uint4* tmask) {
   const uint32_t iters = d.eta >> 8;
   uint32_t cnt = 0;
   for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
@@ -133,8 +147,9 @@ __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint
     uint4 v[8];
     uint32_t t[8];
     load_group<TOUCH>(r0, base, tb, it0, m, lane, v, t);
-    cnt += proc_group<ADV, HOT, TOUCH>(r0, g, base, tb, my, it0, m, lane, c, v, t);
+    cnt += fast_group<ADV, HOT, TOUCH>(r0, g, base, tb, it0, m, lane, c, tmask, v, t);
   }
+  if (HOT) hot_bits(d, r0, base, cnt, my, lane, c);
   return cnt;
 }
 
@@ -171,6 +186,7 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
                                                          const __grid_constant__ StreamArgs a) {
   extern __shared__ __align__(16) uint8_t smask[];
   __shared__ RouterClock sck[ONE ? 1 : kMaxBatch];
+  __shared__ uint4 stm[ONE && TOUCH ? 256 : 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* my = smask + (size_t)wid * (d.eta >> 3);
   const uint64_t count = a.se_count ? a.se_count : ((uint64_t)d.r << d.q);
@@ -188,13 +204,18 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
     for (int j = threadIdx.x; j < a.n; j += blockDim.x) sck[j] = router_clock(a.tm[j]);
     __syncthreads();
   }
+  if (ONE && TOUCH) {
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) stm[j] = touch_mask_entry((uint32_t)j);
+    __syncthreads();
+  }
 
   for (uint64_t se = a.se0 + (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < se_end; se += wstride) {
     const uint64_t base = (se << d.log2_eta) >> 3;  // in 8-recorder units
     uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane : nullptr;
     uint32_t cnt = 0;
     if (ONE) {
-      cnt = one_router_se<ADV, HOT, TOUCH>(d, reinterpret_cast<uint4*>(a.routers[0]), g, base, tb, my, lane, c);
+      uint4* const r0 = reinterpret_cast<uint4*>(a.routers[0]);
+      cnt = one_router_se<ADV, HOT, TOUCH>(d, r0, g, base, tb, my, lane, c, stm);
     } else {
       for (uint32_t it = 0; it < iters; ++it) {
         const uint64_t at = base + it * 32 + lane;
@@ -356,10 +377,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   uint8_t* masks = reinterpret_cast<uint8_t*>(smc + (TABLES ? 2048 : 0));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* my = masks + (size_t)wid * (d.eta >> 3);
-  if (TABLES) {
+  __shared__ uint4 stm[256];   // touch masks (touch_mask_entry)
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) stm[i] = touch_mask_entry((uint32_t)i);
+  if (TABLES)
     for (int i = threadIdx.x; i < 2048; i += blockDim.x) sT[i] = s.tables[i];
-    __syncthreads();
-  }
+  __syncthreads();
   // the warp's first estimator: its recorders are loaded before the wait (no earlier grid of
   // the slot writes them), its touch bytes after it
   const uint32_t iters = d.eta >> 8;
@@ -439,20 +461,22 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (u < (int)m0) t[u] = tb[u * 32];
-    uint32_t cnt = proc_group<true, true, true>(r0, g, base, tb, my, 0, m0, lane, c, v, t);
+    uint32_t cnt = fast_group<true, true, true>(r0, g, base, tb, 0, m0, lane, c, stm, v, t);
     for (uint32_t it0 = 8; it0 < iters; it0 += 8) {
       const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
       load_group<true>(r0, base, tb, it0, m, lane, v, t);
-      cnt += proc_group<true, true, true>(r0, g, base, tb, my, it0, m, lane, c, v, t);
+      cnt += fast_group<true, true, true>(r0, g, base, tb, it0, m, lane, c, stm, v, t);
     }
+    hot_bits(d, r0, base, cnt, my, lane, c);
     finish(e, se, cnt, w0);
     e += wstride;
   }
   for (; e < a.count; e += wstride) {
     const uint64_t se = a.se0 + e;
     const uint4 w0 = first_pair(e);
-    const uint32_t cnt =
-        one_router_se<true, true, true>(d, r0, g, (se << d.log2_eta) >> 3, a.touch + e * tstep + lane, my, lane, c);
+    const uint64_t base = (se << d.log2_eta) >> 3;
+    uint8_t* tb = a.touch + e * tstep + lane;
+    const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, base, tb, my, lane, c, stm);
     finish(e, se, cnt, w0);
   }
 }
