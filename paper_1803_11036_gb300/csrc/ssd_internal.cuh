@@ -197,10 +197,12 @@ __device__ __forceinline__ uint32_t out_range2(uint32_t x, uint32_t lo2, uint32_
   return umin2(umax2(umin2(x, hi2), lo2) ^ x, 0x00010001u);
 }
 // 1 in each half of x outside the window, 0 inside (so a sum of these words counts the recorders
-// outside, per half, in 16-bit fields). c.wrap is the same for the whole grid.
+// outside, per half, in 16-bit fields). WRAP = c.wrap, chosen once per group by the caller (it is
+// the same for the whole grid), so the common case pays for one range only.
+template <bool WRAP>
 __device__ __forceinline__ uint32_t out2(uint32_t x, const Clock& c) {
   uint32_t o = out_range2(x, c.lo2, c.hi2);
-  if (c.wrap) o &= out_range2(x, 0u, c.tm2);
+  if (WRAP) o &= out_range2(x, 0u, c.tm2);
   return o;
 }
 // Whether any of the 8 recorders holds the stamp xe (a zero half in x ^ xe).
@@ -334,10 +336,21 @@ __device__ __forceinline__ void set_touch(uint32_t* bits, uint64_t bit, bool ok)
   }
 }
 
+// Position of recorder x's bit among its estimator's eta touch bits. For eta >= 256 the streaming
+// kernels give vector vi = x / 8 of an estimator to lane vi mod 32 as its (vi / 32)-th vector, so
+// the byte of vector vi is stored at (vi mod 32) * (eta / 256) + vi / 32: a lane's bytes are
+// contiguous, read with one load and cleared with one store. For eta < 256 a lane takes one
+// vector and the byte stays at vi.
+__device__ __forceinline__ uint32_t touch_pos(const Dims& d, uint32_t x) {
+  if (d.log2_eta < 8u) return x;
+  const uint32_t vi = x >> 3;
+  return ((((vi & 31u) << (d.log2_eta - 8u)) | (vi >> 5)) << 3) | (x & 7u);
+}
+
 // Algorithm 2 for the estimators [se0, se0 + count) only (one chunk, inside one
 // row or whole rows): the recorder a pair sets to 0 is marked in `bits` instead
 // (router base jbase = router * count; estimator se0 + e, recorder x -> bit
-// (jbase + e) * eta + x). sT holds both table sets (2048 words). `live` = false
+// (jbase + e) * eta + touch_pos(x)). sT holds both table sets (2048 words). `live` = false
 // makes the call a no-op (a lane past the end of the pairs; with CM == 1 every
 // lane calls).
 template <int CM>
@@ -355,7 +368,7 @@ __device__ __forceinline__ void touch_pair(uint32_t* bits, uint64_t jbase, uint3
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
     const bool ok = live && e < count;
     if (ok && x == 0xFFFFFFFFu) x = tab_hash(sT, oip) & (d.eta - 1u);
-    const uint64_t bit = ((jbase + e) << d.log2_eta) | x;
+    const uint64_t bit = ((jbase + e) << d.log2_eta) | touch_pos(d, x);
     set_touch<CM>(bits, bit, ok && in_bounds(d, bit < d.touch_bits));
   }
 }
@@ -373,7 +386,7 @@ __device__ __forceinline__ void touch_packed(uint32_t* bits, uint32_t cip, uint3
       col = ((sh < 32u ? (cip >> sh) : 0u) ^ c0) & d.col_mask;
     }
     const uint64_t e = (((uint64_t)i << d.q) | col) - se0;
-    const uint64_t bit = (e << d.log2_eta) | x;
+    const uint64_t bit = (e << d.log2_eta) | touch_pos(d, x);
     const bool ok = live && e < count;
     set_touch<CM>(bits, bit, ok && in_bounds(d, bit < d.touch_bits && x < d.eta));
   }
@@ -394,7 +407,8 @@ cudaError_t launch_touch_packed(const Dims& d, const uint4* vec, uint64_t nvec, 
 // ---- per-chunk touch lists of the fused slot (ssd_scan.cu) ----
 // Algorithm 2 for every pair of the batch, once per slot, sorted by chunk: chunk c covers the
 // estimators [c * count, (c + 1) * count) of every router, and the touch of router j, estimator
-// se, recorder x has the bit ((j * count + se - c * count) << log2_eta) | x of that chunk's bits.
+// se, recorder x has the bit ((j * count + se - c * count) << log2_eta) | touch_pos(x) of that
+// chunk's bits.
 // Chunk 0's bits are set directly in `touch0`; the bit index of every touch of chunk c >= 1 is
 // appended to list c (ent + (c - 1) * cap, fill[c] entries). A pair adds at most one touch per
 // row, so a list of a chunk inside one row never holds more than the batch's pairs.

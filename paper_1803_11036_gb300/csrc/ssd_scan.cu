@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_lists(const Dims d, const uint32_t* 
         }
         const uint64_t se = ((uint64_t)i << d.q) | col;
         const uint32_t c = (uint32_t)(se >> a.log2_count);
-        const uint64_t bit = ((jbase + (se & (count - 1))) << d.log2_eta) | xr;
+        const uint64_t bit = ((jbase + (se & (count - 1))) << d.log2_eta) | touch_pos(d, xr);
         if (!write) set_touch<CM>(a.touch0, bit, in && c == 0 && in_bounds(d, bit < d.touch_bits));
         const uint32_t key = (in && c != 0) ? c : 0xFFFFFFFFu;
         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key);

@@ -66,53 +66,96 @@ __device__ __forceinline__ uint32_t take_touch(uint8_t* p) {
 }
 
 // Recorder vectors it0 .. it0+m-1 (m <= 8, 32 lanes x 8 recorders each) of the
-// estimator at `base` and, with TOUCH, their touch bytes. All loads of a group
-// are issued before any store of it (a store in between could alias the next
-// load and serialise them).
-template <bool TOUCH>
-__device__ __forceinline__ void load_group(const uint4* r0, uint64_t base, const uint8_t* tb, uint32_t it0, uint32_t m,
-                                           int lane, uint4 (&v)[8], uint32_t (&t)[8]) {
+// estimator at `base`. All loads of a group are issued before any store of it (a
+// store in between could alias the next load and serialise them).
+__device__ __forceinline__ void load_group(const uint4* r0, uint64_t base, uint32_t it0, uint32_t m, int lane,
+                                           uint4 (&v)[8]) {
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    if (u < (int)m) {
-      v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
-      if (TOUCH) t[u] = tb[(it0 + u) * 32];
-    }
-  }
+  for (int u = 0; u < 8; ++u)
+    if (u < (int)m) v[u] = __ldcs(r0 + base + (it0 + u) * 32 + lane);
 }
 
-// The loaded group of one router's stamps: touch bits applied (those recorders take the stamp tm,
-// distance 0; the masks come from the table tmask, built by touch_mask_entry; the bits are
-// cleared), the state written to g, the recorders inside the window counted (out2), and the
-// vectors that changed - a recorder set by a touch or, with ADV, one whose distance reaches 65535
-// at this advance (it becomes kNever; any_eq8 tests the whole vector first) - written back. No
-// window bits are written: the caller builds them with group_bits only for a hot estimator.
-// Returns the lane's count of recorders inside the window.
-template <bool ADV, bool HOT, bool TOUCH>
-__device__ __forceinline__ uint32_t fast_group(uint4* r0, uint4* g, uint64_t base, uint8_t* tb, uint32_t it0,
-                                               uint32_t m, int lane, const Clock& c, const uint4* tmask,
-                                               uint4 (&v)[8], const uint32_t (&t)[8]) {
+// kNever into the recorders of v holding the stamp xe. Out of line: a recorder expires once in
+// 65535 slots, and a call keeps this from being if-converted into every vector's path.
+__device__ __noinline__ uint4 expire_vec(uint4 v, uint32_t xe2) {
+  return make_uint4(v.x | __vcmpeq2(v.x, xe2), v.y | __vcmpeq2(v.y, xe2), v.z | __vcmpeq2(v.z, xe2),
+                    v.w | __vcmpeq2(v.w, xe2));
+}
+
+// The touch bytes of a lane's m vectors (m = 1, 2, 4 or 8; byte u of the result for its u-th
+// vector), contiguous and aligned to m bytes by touch_pos, and their clearing.
+__device__ __forceinline__ uint64_t load_touch(const uint8_t* p, uint32_t m) {
+  if (m == 8) return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+  if (m == 4) return __ldcg(reinterpret_cast<const unsigned int*>(p));
+  if (m == 2) return __ldcg(reinterpret_cast<const unsigned short*>(p));
+  return __ldcg(p);
+}
+// (cleared only when `any`, by a predicated store: no branch around it)
+__device__ __forceinline__ void clear_touch(uint8_t* p, uint32_t m, bool any) {
+  const uint32_t c = any ? 1u : 0u;
+  if (m == 8)
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %1, 0; @q st.global.u64 [%0], 0; }" :: "l"(p), "r"(c) : "memory");
+  else if (m == 4)
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %1, 0; @q st.global.u32 [%0], 0; }" :: "l"(p), "r"(c) : "memory");
+  else if (m == 2)
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %1, 0; @q st.global.u16 [%0], 0; }" :: "l"(p), "r"(c) : "memory");
+  else
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %1, 0; @q st.global.u8 [%0], 0; }" :: "l"(p), "r"(c) : "memory");
+}
+
+// __stcs(p, v) when c: a predicated store, so the lanes that write and those that do not need no
+// branch (and no reconvergence) between them.
+__device__ __forceinline__ void stcs_if(uint4* p, uint4 v, bool c) {
+  asm volatile("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q st.global.cs.v4.u32 [%0], {%1, %2, %3, %4}; }"
+               :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(c ? 1u : 0u) : "memory");
+}
+
+// The loaded group of one router's stamps: touch bits applied (tw: the group's touch bytes, from
+// load_touch; those recorders take the stamp tm, distance 0, through the masks of the table tmask,
+// built by touch_mask_entry; the caller clears the bytes), the state written to g, the recorders
+// inside the window counted (out2), and the vectors that changed written back: a recorder set by
+// a touch, or, with ADV, one whose distance reaches 65535 at this advance (it becomes kNever).
+// The common path has no divergent branch: touched vectors are stored by predicated stores, and
+// the expiry (any_eq8 per vector) is taken once for the group behind a warp vote, reading back the
+// vectors it rewrites. No window bits are written: the caller builds them with group_bits only
+// for a hot estimator. Returns the lane's count of recorders inside the window.
+template <bool ADV, bool HOT, bool TOUCH, bool WRAP>
+__device__ __forceinline__ uint32_t fast_group_w(uint4* r0, uint4* g, uint64_t base, uint32_t it0, uint32_t m,
+                                                 int lane, const Clock& c, const uint4* tmask, uint4 (&v)[8],
+                                                 uint64_t tw) {
   uint32_t out = 0;   // recorders outside the window, per half, in two 16-bit fields
+  uint32_t expiring = 0;   // bit u: vector u holds a recorder with the stamp xe
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     if (u < (int)m) {
       const uint64_t at = base + (it0 + u) * 32 + lane;
-      bool dirty = false;
-      if (TOUCH && t[u]) {
-        v[u] = set_masked(v[u], tmask[t[u]], c.tm2);
-        tb[(it0 + u) * 32] = 0;
-        dirty = true;
+      if (TOUCH) {
+        const uint32_t t = (uint32_t)(tw >> (8 * u)) & 0xFFu;
+        v[u] = set_masked(v[u], tmask[t], c.tm2);
+        stcs_if(r0 + at, v[u], t != 0u);
       }
       if (g) __stcs(g + at, v[u]);
-      if (HOT) out += out2(v[u].x, c) + out2(v[u].y, c) + out2(v[u].z, c) + out2(v[u].w, c);
-      if (ADV && any_eq8(v[u], c.xe2)) {
-        v[u] = or8(v[u], expire8(v[u], c));
-        dirty = true;
+      if (HOT) out += out2<WRAP>(v[u].x, c) + out2<WRAP>(v[u].y, c) + out2<WRAP>(v[u].z, c) + out2<WRAP>(v[u].w, c);
+      if (ADV) expiring |= any_eq8(v[u], c.xe2) ? 1u << u : 0u;
+    }
+  }
+  if (ADV && __any_sync(kFull, expiring != 0u)) {   // once in 65535 slots per recorder
+    for (uint32_t u = 0; u < m; ++u) {
+      if ((expiring >> u) & 1u) {
+        const uint64_t at = base + (it0 + u) * 32 + lane;
+        __stcs(r0 + at, expire_vec(__ldcg(r0 + at), c.xe2));   // the lane's own (touched) vector
       }
-      if (dirty) __stcs(r0 + at, v[u]);
     }
   }
   return 8u * m - (out & 0xFFFFu) - (out >> 16);
+}
+// fast_group with the window's form chosen once for the group (c.wrap is the same for the grid).
+template <bool ADV, bool HOT, bool TOUCH>
+__device__ __forceinline__ uint32_t fast_group(uint4* r0, uint4* g, uint64_t base, uint32_t it0, uint32_t m,
+                                               int lane, const Clock& c, const uint4* tmask, uint4 (&v)[8],
+                                               uint64_t tw) {
+  if (HOT && c.wrap) return fast_group_w<ADV, HOT, TOUCH, true>(r0, g, base, it0, m, lane, c, tmask, v, tw);
+  return fast_group_w<ADV, HOT, TOUCH, false>(r0, g, base, it0, m, lane, c, tmask, v, tw);
 }
 
 // The window bits of a group fast_group has processed, to `my`, from the recorders read again one
@@ -136,7 +179,7 @@ __device__ __forceinline__ void hot_bits(const Dims& d, const uint4* r0, uint64_
 
 // One estimator of one router, all eta recorders (eta >= 256), in groups of 8 vectors per lane:
 // load_group then fast_group, then the window bits only when the warp's count reaches the
-// threshold (pool_if_hot pools it). tb: this lane's byte of the estimator's touch bits.
+// threshold (pool_if_hot pools it). tb: this lane's touch bytes of the estimator (touch_pos).
 template <bool ADV, bool HOT, bool TOUCH>
 __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint4* g, uint64_t base, uint8_t* tb,
                                                   uint8_t* my, int lane, const Clock& c, const uint4* tmask) {
@@ -145,9 +188,10 @@ __device__ __forceinline__ uint32_t one_router_se(const Dims& d, uint4* r0, uint
   for (uint32_t it0 = 0; it0 < iters; it0 += 8) {
     const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
     uint4 v[8];
-    uint32_t t[8];
-    load_group<TOUCH>(r0, base, tb, it0, m, lane, v, t);
-    cnt += fast_group<ADV, HOT, TOUCH>(r0, g, base, tb, it0, m, lane, c, tmask, v, t);
+    load_group(r0, base, it0, m, lane, v);
+    const uint64_t tw = TOUCH ? load_touch(tb + it0, m) : 0ull;
+    cnt += fast_group<ADV, HOT, TOUCH>(r0, g, base, it0, m, lane, c, tmask, v, tw);
+    if (TOUCH) clear_touch(tb + it0, m, tw != 0ull);
   }
   if (HOT) hot_bits(d, r0, base, cnt, my, lane, c);
   return cnt;
@@ -211,7 +255,7 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
 
   for (uint64_t se = a.se0 + (uint64_t)blockIdx.x * (kBlock / 32) + wid; se < se_end; se += wstride) {
     const uint64_t base = (se << d.log2_eta) >> 3;  // in 8-recorder units
-    uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane : nullptr;
+    uint8_t* tb = TOUCH ? a.touch + (se - a.se0) * (d.eta >> 3) + lane * iters : nullptr;   // touch_pos
     uint32_t cnt = 0;
     if (ONE) {
       uint4* const r0 = reinterpret_cast<uint4*>(a.routers[0]);
@@ -229,7 +273,7 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
           for (int u = 0; u < G; ++u) {
             if (u < m) {
               v[u] = __ldcs(reinterpret_cast<uint4*>(a.routers[n0 + u]) + at);
-              if (TOUCH) t[u] = tb[(uint64_t)(n0 + u) * tstride + it * 32];
+              if (TOUCH) t[u] = tb[(uint64_t)(n0 + u) * tstride + it];
             }
           }
 #pragma unroll
@@ -239,7 +283,7 @@ __global__ void __launch_bounds__(kBlock, ONE ? 4 : 3) k_stream_large(const Dims
               bool dirty = false;
               if (TOUCH && t[u]) {
                 v[u] = set8(v[u], t[u], rc.tm2);
-                tb[(uint64_t)(n0 + u) * tstride + it * 32] = 0;
+                tb[(uint64_t)(n0 + u) * tstride + it] = 0;
                 dirty = true;
               }
               mv = min8(mv, stamps ? flip8(v[u], rc.tm2) : v[u]);
@@ -388,11 +432,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   const uint32_t m0 = iters < 8u ? iters : 8u;
   const uint64_t tstep = d.eta >> 3;   // touch bytes per estimator
   uint4 v[8];
-  uint32_t t[8];
   const uint64_t e_first = (uint64_t)blockIdx.x * (kBlock / 32) + wid;
   if (e_first < a.count)
-    load_group<false>(reinterpret_cast<const uint4*>(a.router), ((a.se0 + e_first) << d.log2_eta) >> 3, nullptr, 0,
-                      m0, lane, v, t);
+    load_group(reinterpret_cast<const uint4*>(a.router), ((a.se0 + e_first) << d.log2_eta) >> 3, 0, m0, lane, v);
   asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous grid has completed
   // the router's clock (moved on only after the slot's last launch)
   const uint32_t tm = *a.tm;
@@ -455,17 +497,18 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
   uint64_t e = e_first;
   if (e < a.count) {   // the prefetched first group, then any further groups
     const uint64_t se = a.se0 + e;
-    uint8_t* tb = a.touch + e * tstep + lane;
+    uint8_t* tb = a.touch + e * tstep + lane * iters;   // touch_pos
     const uint4 w0 = first_pair(e);
     const uint64_t base = (se << d.log2_eta) >> 3;
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (u < (int)m0) t[u] = tb[u * 32];
-    uint32_t cnt = fast_group<true, true, true>(r0, g, base, tb, 0, m0, lane, c, stm, v, t);
+    uint64_t tw = load_touch(tb, m0);
+    uint32_t cnt = fast_group<true, true, true>(r0, g, base, 0, m0, lane, c, stm, v, tw);
+    clear_touch(tb, m0, tw != 0ull);
     for (uint32_t it0 = 8; it0 < iters; it0 += 8) {
       const uint32_t m = iters - it0 < 8u ? iters - it0 : 8u;
-      load_group<true>(r0, base, tb, it0, m, lane, v, t);
-      cnt += fast_group<true, true, true>(r0, g, base, tb, it0, m, lane, c, stm, v, t);
+      load_group(r0, base, it0, m, lane, v);
+      tw = load_touch(tb + it0, m);
+      cnt += fast_group<true, true, true>(r0, g, base, it0, m, lane, c, stm, v, tw);
+      clear_touch(tb + it0, m, tw != 0ull);
     }
     hot_bits(d, r0, base, cnt, my, lane, c);
     finish(e, se, cnt, w0);
@@ -475,7 +518,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_chunk(const Dims d, const Scratch
     const uint64_t se = a.se0 + e;
     const uint4 w0 = first_pair(e);
     const uint64_t base = (se << d.log2_eta) >> 3;
-    uint8_t* tb = a.touch + e * tstep + lane;
+    uint8_t* tb = a.touch + e * tstep + lane * iters;   // touch_pos
     const uint32_t cnt = one_router_se<true, true, true>(d, r0, g, base, tb, my, lane, c, stm);
     finish(e, se, cnt, w0);
   }
