@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-c1", action="store_true", help="skip the leg at the paper's own dimensions")
     ap.add_argument("--touch-chunk-mib", type=int, default=0, help="touch bits per chunk of the fused slot")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--tuning", default="", help="launch configuration as JSON (ssd_tuning fields), "
+                    "set instead of running the autotuner, e.g. to profile the configuration a run chose")
     return ap.parse_args()
 
 
@@ -208,10 +210,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, chunk: int, path: str | None = None):
+def profiled_traffic(workload: str, chunk: int, path: str | None = None, collect: int | None = None):
     """DRAM bytes per chunk launch of the streaming pass from the committed ncu summary, if
-    the kernel source has not changed since it was captured and the launch covers as many
-    estimators as the captured one."""
+    the kernel source has not changed since it was captured, the launch covers as many
+    estimators as the captured one and, when `collect` is given, the summary was taken on the
+    same touch-collection route (ssd_tuning's collect_touches)."""
     path = path or os.path.join(ROOT, "profiles", f"chunk_pass_{workload}.md")
     try:
         text = open(path).read()
@@ -222,6 +225,10 @@ def profiled_traffic(workload: str, chunk: int, path: str | None = None):
     c = re.search(r"chunk_estimators:\s*([0-9]+)", text)
     if not m or not h or not c or h.group(1) != kernel_source_hash() or int(c.group(1)) != chunk:
         return None
+    if collect is not None:
+        r = re.search(r"collect_touches:\s*([0-9]+)", text)
+        if not r or int(r.group(1)) != collect:
+            return None
     return float(m.group(1))
 
 
@@ -650,6 +657,9 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(dev)
     default_tuning = ctx.tuning
     tune_s = 0.0
+    if args.tuning:        # a stated configuration (the autotuner does not run)
+        ctx.tuning = json.loads(args.tuning)
+        args.no_tune = True
     if not args.no_tune:   # launch configuration picked by measurement on the first slot
         t0 = time.perf_counter()
         ctx.autotune(routers, slot_dev[0], None, reps=3, stream=stream)
@@ -785,7 +795,7 @@ def run_ours(args, world, rank, local):
         chunk *= 2
     n_chunks = -(-n_se // chunk)
     peak, peak_kind = measured_peak()
-    traffic = profiled_traffic(args.workload, chunk)
+    traffic = profiled_traffic(args.workload, chunk, collect=tuned["collect_touches"])
     steps = step_rooflines(pk=tr_pk, scan_ms=scan_ms, scan_pk=timed_pk / args.steps, slot_pass=slot_pass,
                            slot_tail=slot_tail, close_pass=close_pass, close_tail=close_tail,
                            rec_bytes=rec_bytes, r=r, peak=peak)
@@ -887,7 +897,8 @@ def run_ours(args, world, rank, local):
                    "k": k, "eta": eta, "q": prm["q"], "r": r, "delta": prm["delta"], "theta": prm["theta"],
                    "window_filled_slots": fill, "l2": "inputs larger than L2: the 5 GiB RSEA is streamed every "
                    "step and each step scans a distinct slice",
-                   "tuning": tuned, "tuned_by": "default" if args.no_tune else "ssd_autotune on the first slot",
+                   "tuning": tuned, "tuned_by": ("--tuning" if args.tuning else "default") if args.no_tune
+                   else "ssd_autotune on the first slot",
                    "tune_s": round(tune_s, 2)},
         "default_configuration": default_leg,
         "gbps_at_800B": gbps(value),

@@ -39,6 +39,10 @@ def test_profile_traffic_needs_matching_code_and_chunk(tmp_path):
                     "chunk_estimators: 131072\n")
     assert bench.profiled_traffic("w", 131072, str(prof)) is None          # the kernel changed since
     assert bench.profiled_traffic("no_such_workload", 131072) is None
+    prof.write_text(f"traffic_bytes_per_launch: 1.13e9\nkernel_source_sha256_16: {bench.kernel_source_hash()}\n"
+                    "chunk_estimators: 131072\ncollect_touches: 1\n")
+    assert bench.profiled_traffic("w", 131072, str(prof), collect=1) == 1.13e9
+    assert bench.profiled_traffic("w", 131072, str(prof), collect=0) is None   # another route
 
 
 def test_code_tokens_ignore_comments_not_strings():
