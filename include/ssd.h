@@ -331,14 +331,16 @@ SSD_API int ssd_set_trace(ssd_ctx* ctx, void* ev_start, void* ev_pass, void* ev_
  * per chunk, double-buffered) stay in L2; a side stream collects the touches of
  * chunk c+1 while the streaming pass applies those of chunk c (recorder := 0,
  * Sec. 4.1), merges, extracts the hot estimators and advances. Every recorder
- * is read and written once per slot and no random DRAM write remains. When the
- * routers' touch bits would need more than 16 chunks the call runs
- * ssd_scan_batch and ssd_close_slot instead (same result).
- * One router with eta >= 256 (unless SSD_SLOT_CHUNKED) uses one stream: chunk
- * 0's bits are collected by one launch, then the streaming kernel of each chunk,
- * between estimators, also hashes a share of the pairs and collects the next
- * chunk's bits, so the collection fills the memory stalls of the stream; up to
- * 32 chunks. */
+ * is read once per slot; only the vectors holding a touched (or expiring)
+ * recorder are written, and no random DRAM write remains. When the routers'
+ * touch bits would need more than 16 chunks the call runs ssd_scan_batch and
+ * ssd_close_slot instead (same result).
+ * One router with eta >= 256 (unless SSD_SLOT_CHUNKED) uses one stream: the
+ * pairs are hashed once per slot (into per-chunk touch lists, or into packed
+ * hashes with ssd_tuning's collect_touches = 1) and chunk 0's bits set by that
+ * launch or the next; then the streaming kernel of each chunk, between
+ * estimators, sets the next chunk's bits, so the collection fills the memory
+ * stalls of the stream; up to 32 chunks. */
 SSD_API int ssd_slot(ssd_ctx* ctx, ssd_sketch* const* routers, const uint32_t* const* d_pairs,
                      const uint64_t* n_pairs, int n, ssd_sketch* global, uint32_t* d_ips, uint32_t* d_rk,
                      uint64_t cap, uint64_t* d_n_out, void* stream);
