@@ -343,17 +343,64 @@ class OracleSlots:
         self.T = tg.Traffic(**S["traffic"])
         self.pipe = oracle.Pipeline(self.p, self.tabs, self.T.routers)
         self.t = 0
+        self.seconds = {"advance": 0.0, "scan": 0.0, "merge": 0.0, "regain": 0.0}
 
     def step(self) -> int:
+        """One slot of the oracle's pipeline (oracle.Pipeline.step's order: advance when t > 0,
+        scan every router, merge, regain), each step timed on its own."""
+        import oracle
+        pipe, clock = self.pipe, time.perf_counter
         pairs = self.T.slot(self.t)
         self.t += 1
-        self.pipe.step(pairs, "pruned")
+        t0 = clock()
+        pipe.t += 1
+        if pipe.t > 0:
+            for sk in pipe.routers:
+                oracle.advance(pipe.p, sk)
+        t1 = clock()
+        for sk, pr in zip(pipe.routers, pairs):
+            oracle.scan(pipe.p, pipe.tables, sk, pr)
+        t2 = clock()
+        pipe.global_sk = oracle.merge(pipe.p, pipe.routers)
+        t3 = clock()
+        oracle.regain(pipe.p, pipe.tables, pipe.global_sk, "pruned")
+        t4 = clock()
+        for k, dt in zip(("advance", "scan", "merge", "regain"), (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+            self.seconds[k] += dt
         return sum(len(x) for x in pairs)
+
+
+def cpu_model() -> str:
+    """The host CPU's model as /proc/cpuinfo names it (x86: model name; Arm: implementer and part
+    numbers), else the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    m = re.search(r"^model name\s*:\s*(.+)$", info, re.M)
+    if m:
+        return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+    if imp and part:
+        return f"{platform.machine()} (CPU implementer {imp.group(1)}, part {part.group(1)})"
+    return platform.machine()
+
+
+def oracle_steps(o: OracleSlots, packets: int, slots: int) -> dict:
+    """Each oracle step's share of the timed slots: the scan per packet, the others per slot."""
+    sec = o.seconds
+    return {"scan_ns_per_packet": round(sec["scan"] / max(packets, 1) * 1e9, 2),
+            "advance_ms_per_slot": round(sec["advance"] / max(slots, 1) * 1e3, 2),
+            "merge_ms_per_slot": round(sec["merge"] / max(slots, 1) * 1e3, 2),
+            "regain_ms_per_slot": round(sec["regain"] / max(slots, 1) * 1e3, 2)}
 
 
 def cpu_baseline(W: dict, budget_s: float = 12.0, min_slots: int = 3) -> dict:
     """The oracle, as it stands, on the bench's own workload: slots until `budget_s` has passed
-    (at least min_slots), the window starting empty."""
+    (at least min_slots), the window starting empty; also each step's share: the scan in ns per
+    packet, the advance, merge and regain in ms per slot."""
     o = OracleSlots(W)
     pk, slots = 0, 0
     t0 = time.perf_counter()
@@ -363,7 +410,8 @@ def cpu_baseline(W: dict, budget_s: float = 12.0, min_slots: int = 3) -> dict:
     dt = time.perf_counter() - t0
     return {"value": round(pk / dt / 1e6, 4), "unit": "Mpps", "cores": 1, "kind": "oracle",
             "sample": f"{slots} slots of {o.desc}", "seconds": round(dt, 2),
-            "host_cpus": os.cpu_count()}
+            "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+            "steps": dict(oracle_steps(o, pk, slots), note="the first slot has no advance (the window starts empty)")}
 
 
 def run_reference(args, world, rank):
@@ -379,6 +427,7 @@ def run_reference(args, world, rank):
     o = OracleSlots(W)
     for _ in range(args.warmup):
         o.step()
+    o.seconds = dict.fromkeys(o.seconds, 0.0)
     t0 = time.perf_counter()
     pk = 0
     for _ in range(args.steps):
@@ -390,7 +439,8 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": {"workload": args.workload, "sample": o.desc},
             "cpu_baseline": {"value": round(v, 4), "unit": "Mpps", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} slots of {o.desc}"},
+                             "sample": f"{args.steps} slots of {o.desc}", "cpu_model": cpu_model(),
+                             "steps": oracle_steps(o, pk, args.steps)},
             "e2e": {"value": round(v, 4), "unit": "Mpps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

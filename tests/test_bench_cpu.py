@@ -75,3 +75,16 @@ def test_step_rooflines_split():
     fast = bench.step_rooflines(pk=6.25e6, scan_ms=1.0, scan_pk=6.25e6, slot_pass=[1.701], slot_tail=[0.1],
                                 close_pass=[1.7], close_tail=[0.1], rec_bytes=1e9, r=5, peak=6000.0)
     assert fast["scan_in_slot"]["target_met"] is True
+
+
+def test_cpu_baseline_reports_each_oracle_step():
+    import trafficgen as tg
+    r = bench.cpu_baseline(tg.workload("tiny"), budget_s=0.2, min_slots=3)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0 and r["cpu_model"]
+    st = r["steps"]
+    for key in ("scan_ns_per_packet", "advance_ms_per_slot", "merge_ms_per_slot", "regain_ms_per_slot"):
+        assert st[key] >= 0
+    n = int(r["sample"].split()[0])
+    # the steps are parts of the timed slots
+    per_slot_ms = st["advance_ms_per_slot"] + st["merge_ms_per_slot"] + st["regain_ms_per_slot"]
+    assert per_slot_ms * n / 1e3 <= r["seconds"] * 1.05 + 0.05
