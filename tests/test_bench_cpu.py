@@ -88,3 +88,11 @@ def test_cpu_baseline_reports_each_oracle_step():
     # the steps are parts of the timed slots
     per_slot_ms = st["advance_ms_per_slot"] + st["merge_ms_per_slot"] + st["regain_ms_per_slot"]
     assert per_slot_ms * n / 1e3 <= r["seconds"] * 1.05 + 0.05
+
+
+def test_tuning_flag_parses_a_stated_configuration(monkeypatch):
+    import json
+    t = {"touch_chunk_bytes": 67108864, "scan_unroll": 8, "collect_touches": 1}
+    monkeypatch.setattr("sys.argv", ["bench.py", "--tuning", json.dumps(t), "--steps", "2"])
+    args = bench.parse()
+    assert json.loads(args.tuning) == t and args.steps == 2 and not args.no_tune
