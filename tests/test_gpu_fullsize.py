@@ -1,4 +1,5 @@
-"""Exact parity at the full size of the benchmark workload, on the route bench.py times.
+"""Exact parity at the full size of the benchmark workload, on the routes bench.py times (the
+default launch configuration, and the pre-hashed route the autotuner also picks for it).
 
 Workload: one core-link router, 6.25 M packets per slot, eta = 2^11, q = 18, r = 5 (a 5 GiB RSEA),
 k = 60, theta = 1024, run for k + 4 slots so the window rolls over.
@@ -100,3 +101,45 @@ def test_corelink_full_size_bench_route_exact():
     assert ra.slot == rb.slot == slots
     ctx_a.close()
     ctx_b.close()
+
+
+def test_corelink_full_size_prehashed_route_exact():
+    """The same workload at full size on the other route the autotuner picks for it: pre-hashed
+    pairs re-read by every chunk launch (collect_touches 1) with 64 MiB touch chunks, five chunk
+    launches per slot, scan unroll 8. Six slots (the window not yet full, so every slot's list is
+    that of slots 0..t): every recorder of the router after each slot's close in blocks, the list
+    and its R_k at the last slot entry by entry, and every recorder at the end."""
+    import torch
+    W = tg.workload("corelink_c2")
+    prm = W["params"]
+    slots = 6
+    tabs = tg.hash_tables(W["hash_seed"])
+    T = tg.traffic_for(W)
+    ctx = ssd.Context(ssd.make_params(prm), tabs)
+    ctx.tuning = dict(touch_chunk_bytes=64 << 20, collect_touches=1, scan_unroll=8)
+    router = ctx.sketch()
+    n_rec = ctx.sketch_bytes // 2
+    p_lit = oracle.params(prm)
+    sk = oracle.new_sketch(p_lit)
+    rng = np.random.default_rng(11)
+    got = None
+    for t in range(slots):
+        pairs = T.slot(t)[0]
+        if t:
+            oracle.advance(p_lit, sk)
+            off = int(rng.integers(0, n_rec - BLOCK))
+            assert np.array_equal(router.export(off, BLOCK), sk[off:off + BLOCK]), (t, off)
+        oracle.scan(p_lit, tabs, sk, pairs)
+        dev = to_dev(pairs)
+        got = ctx.slot([router], [dev])
+        del dev
+    torch.cuda.synchronize()
+    want = oracle.regain(p_lit, tabs, sk, "pruned")
+    _assert_list(got, want, f"slot {slots - 1}, pre-hashed route, literal list")
+    assert len(want["ips"]) > 0
+    oracle.advance(p_lit, sk)
+    step = 1 << 28
+    for off in range(0, n_rec, step):
+        c = min(step, n_rec - off)
+        assert np.array_equal(router.export(off, c), sk[off:off + c]), ("router", off)
+    ctx.close()
